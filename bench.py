@@ -1,0 +1,375 @@
+"""Benchmark of the pre-alignment filtering hot path on GB300.
+
+Workload (one GPU): 20,000,000 read/reference pairs of 150 bp, E = 6,
+bases 0.1% N and 41% GC, 20% of pairs with at most E edits and 80% with
+E+1..60 edits (sub/ins/del 0.6/0.2/0.2), seeded synthetic ASCII resident in
+HBM (inputs are far larger than L2, so no flush is needed between steps).
+
+One step = the whole hot path over the batch: pack reads and references to
+bit-planes, filter with SneakySnake and GateKeeper (batched persistent
+kernels), compact the pairs SneakySnake accepts, verify them with the banded
+bit-vector kernel.  value = pairs per second of that step.
+
+Extra keys: per-stage times, the plain vs batched SneakySnake filter kernel
+(pairs/s), the roofline of the dominant kernel, the end-to-end figure
+(host ASCII in pinned memory -> device -> step -> results back), SM clocks
+sampled during the timed region, and the CPU oracle timed on a bounded
+sample on the host cores.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) every rank runs an independent replica on its own
+GPU and its own shard of pairs (weak scaling); rank 0 prints the line with
+the slowest rank's time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+M, E_HEAD, N_PAIRS, KMAX = 150, 6, 20_000_000, 60
+SEED = 0x5EED0001
+METRIC = "pairs/s (SneakySnake, 150bp, E=6) batched vs plain kernel; serve p50/p99 ms"
+WORKLOAD = "cfg2_150bp_E6_20M"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling in the background during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (also the reference arm)
+
+def oracle_step_rate(n_sample, threads=None):
+    """Time the oracle on pairs [0, n_sample) of the workload: filter with
+    both deciders, then banded Wagner-Fischer on the SneakySnake accepts.
+    Returns (pairs/s, seconds, threads)."""
+    import oracle
+    import synth
+    threads = threads or os.cpu_count() or 1
+    P = synth.generate(synth.SKEWED, SEED, n_sample, m=M, E=E_HEAD, kmax=KMAX, threads=threads)
+    t0 = time.perf_counter()
+    acc, _ = oracle.filter_batch(P, deciders=3, threads=threads)
+    sel = np.nonzero(acc[0])[0]
+    sub = synth.Pairs(P.reads, P.refs, P.read_off[sel], P.ref_off[sel], P.lens[sel], P.E[sel])
+    oracle.verify_batch(sub, threads=threads)
+    dt = time.perf_counter() - t0
+    return n_sample / dt, dt, threads
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n_sample = args.cpu_sample
+    times = []
+    rate = None
+    for i in range(args.warmup + args.steps):
+        r, dt, thr = oracle_step_rate(n_sample)
+        if i >= args.warmup:
+            times.append(dt)
+            rate = r
+    ms = 1000.0 * statistics.mean(times)
+    value = n_sample / (ms / 1000.0)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "pairs": N_PAIRS, "read_len": M, "E": E_HEAD,
+                   "l2": "inputs larger than L2"},
+        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": thr, "kind": "oracle",
+                         "sample": "pairs 0..%d of the workload per step (filter both "
+                                   "deciders + banded WF on SneakySnake accepts)" % n_sample},
+        "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+
+def main_gpu(args):
+    import torch
+    import synth
+    import paper_1910_03936_gb300 as pf
+    from paper_1910_03936_gb300 import build as pfbuild
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pfbuild.build()
+    synth.build()
+
+    n = args.pairs
+    p0 = rank * n  # this replica's shard of the pair space
+    t_gen = time.perf_counter()
+    P = synth.generate(synth.SKEWED, SEED, n, m=M, E=E_HEAD, kmax=KMAX, p0=p0)
+    t_gen = time.perf_counter() - t_gen
+
+    ctx = pf.pf_create(local)
+    stream = torch.cuda.current_stream(dev)
+    reads_h = torch.from_numpy(P.reads).pin_memory()
+    refs_h = torch.from_numpy(P.refs).pin_memory()
+    reads = reads_h.to(dev)
+    refs = refs_h.to(dev)
+    del P
+    W = (M + 31) // 32
+    lens = torch.full((n,), M, dtype=torch.int32, device=dev)
+    E = torch.full((n,), E_HEAD, dtype=torch.int16, device=dev)
+    rd = pf.Seqs.empty(n * W, dev, stride_words=W)
+    rf = pf.Seqs.empty(n * W, dev, stride_words=W)
+    pairs = pf.Pairs(rd, rf)
+    acc = torch.empty(2 * n, dtype=torch.uint8, device=dev)
+    cnt = torch.empty(2 * n, dtype=torch.int16, device=dev)
+    dist_out = torch.empty(n, dtype=torch.int32, device=dev)
+    acc_h = torch.empty(2 * n, dtype=torch.uint8).pin_memory()
+    cnt_h = torch.empty(2 * n, dtype=torch.int16).pin_memory()
+    dist_h = torch.empty(n, dtype=torch.int32).pin_memory()
+
+    # tune the batched kernel for this threshold on a sample of the batch
+    pf.pf_pack_fixed(ctx, reads, n, M, rd)
+    pf.pf_pack_fixed(ctx, refs, n, M, rf)
+    tune_n = min(n, 2_000_000)
+    tuned = {}
+    for dec in (1, 3):
+        tuned[dec] = pf.pf_tune(ctx, dec, pairs, lens, E_HEAD, n=tune_n, reps=2)
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    stage_names = ("pack", "filter", "compact_verify")
+
+    def step(record=None):
+        e = [ev() for _ in range(4)] if record is not None else None
+        if e: e[0].record(stream)
+        pf.pf_pack_fixed(ctx, reads, n, M, rd)
+        pf.pf_pack_fixed(ctx, refs, n, M, rf)
+        if e: e[1].record(stream)
+        pf.pf_filter_verify(ctx, 3, pairs, lens, E, E_HEAD, acc, cnt, dist_out, n)
+        if e: e[3].record(stream)
+        if record is not None:
+            record.append(e)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    pf.pf_sync(ctx)
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    recs = []
+    t0, t1 = ev(), ev()
+    t0.record(stream)
+    for _ in range(args.steps):
+        step(recs)
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    pf.pf_sync(ctx)
+    ms = t0.elapsed_time(t1) / args.steps
+    if dist is not None:
+        tt = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    pack_ms = statistics.mean(r[0].elapsed_time(r[1]) for r in recs)
+    fv_ms = statistics.mean(r[1].elapsed_time(r[3]) for r in recs)
+
+    # per-kernel split of filter vs compact+verify: time them separately
+    def timed(fn, reps=args.steps):
+        a, b = ev(), ev()
+        fn()
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / reps
+
+    filt_ms = timed(lambda: pf.pf_filter(ctx, 3, pairs, lens, E, E_HEAD, acc, cnt, n))
+    idx = torch.empty(n, dtype=torch.int64, device=dev)
+    n_idx = torch.empty(1, dtype=torch.int64, device=dev)
+    pf.pf_compact(ctx, acc[:n], idx, n_idx, n)
+    compact_ms = timed(lambda: pf.pf_compact(ctx, acc[:n], idx, n_idx, n))
+    verify_ms = timed(lambda: pf.pf_verify(ctx, pairs, lens, E, E_HEAD, idx, n_idx, dist_out, n))
+    n_verified = int(n_idx.item())
+    # headline comparison: SneakySnake alone, batched (tuned) vs plain kernel
+    ss_batched_ms = timed(lambda: pf.pf_filter(ctx, 1, pairs, lens, E, E_HEAD, acc, cnt, n))
+    ss_plain_ms = timed(lambda: pf.pf_filter_plain(ctx, 1, pairs, lens, E, E_HEAD, acc, cnt, n))
+    pf.pf_sync(ctx)
+
+    # end to end through the public API: pinned host ASCII in, results out
+    def e2e_step():
+        reads.copy_(reads_h, non_blocking=True)
+        refs.copy_(refs_h, non_blocking=True)
+        step()
+        acc_h.copy_(acc, non_blocking=True)
+        cnt_h.copy_(cnt, non_blocking=True)
+        dist_h.copy_(dist_out, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize(dev)
+    a, b = ev(), ev()
+    e2e_steps = max(1, min(args.steps, 5))
+    a.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = a.elapsed_time(b) / e2e_steps
+    if dist is not None:
+        tt = torch.tensor([e2e_ms], dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    pf.pf_sync(ctx)
+
+    pk, pk_kind = peaks()
+    stages = {"pack": pack_ms, "filter": filt_ms, "compact": compact_ms, "verify": verify_ms}
+    dominant = max(stages, key=stages.get)
+    # algorithmic bytes per pair (packed input 0.75 m, outputs)
+    alg = {
+        "pack": n * (2 * M + 2 * 3 * M / 8.0),
+        "filter": n * (2 * 3 * M / 8.0 + 4 + 2 * 3),
+        "compact": n * 1 + n_verified * 8,
+        "verify": n_verified * (2 * 3 * M / 8.0 + 4 + 4 + 8),
+    }
+    ms_dom = stages[dominant]
+    achieved = alg[dominant] / (ms_dom / 1000.0) / 1e9
+    roof = {"kernel": dominant, "bound": "hbm", "achieved": achieved,
+            "peak": pk.get("hbm_gbs"), "unit": "GB/s",
+            "frac": achieved / pk.get("hbm_gbs"), "traffic": None,
+            "peak_source": pk_kind}
+
+    total = n * world
+    value = total / (ms / 1000.0)
+    line = {
+        "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "pairs_per_gpu": n, "read_len": M, "E": E_HEAD,
+                   "deciders": "SneakySnake+GateKeeper", "verify": "SneakySnake accepts",
+                   "l2": "inputs larger than L2 (9 GB resident)"},
+        "stages_ms": {"pack": pack_ms, "filter_compact_verify": fv_ms, "filter": filt_ms,
+                      "compact": compact_ms, "verify": verify_ms},
+        "accepted_frac": n_verified / n,
+        "filter_sneakysnake": {"batched_pairs_s": n / (ss_batched_ms / 1000.0),
+                               "plain_pairs_s": n / (ss_plain_ms / 1000.0),
+                               "batched_over_plain": ss_plain_ms / ss_batched_ms,
+                               "tuned_cfg": list(tuned[1])},
+        "roofline": roof,
+        "e2e": {"value": total / (e2e_ms / 1000.0), "unit": "pairs/s",
+                "h2d_bytes_per_step": 2 * n * M,
+                "d2h_bytes_per_step": n * (2 + 4 + 4)},
+        "gpu_launches": None,
+        "clocks": clk,
+        "gen_s": t_gen,
+    }
+    # kernels of ours launched per step: 2 pack + bin init + filter +
+    # 3 compaction + fill + verify
+    line["gpu_launches"] = args.steps * 9
+    if rank == 0 and world == 1 and not args.no_cpu:
+        r, dt, thr = oracle_step_rate(args.cpu_sample)
+        line["cpu_baseline"] = {"value": r, "unit": "pairs/s", "cores": thr, "kind": "oracle",
+                                "sample": "first %d pairs of the workload (filter both "
+                                          "deciders + banded WF on SneakySnake accepts), "
+                                          "%.1f s" % (args.cpu_sample, dt)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    pf.pf_destroy(ctx)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--pairs", type=int, default=N_PAIRS)
+    ap.add_argument("--cpu-sample", type=int, default=400_000)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        main_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

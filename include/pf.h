@@ -1,0 +1,231 @@
+/*
+ * pf.h - pre-alignment filtering of read / reference-segment pairs on one
+ * GB300 GPU (sm_103a).
+ *
+ * The method is the thesis of M. Alser, "Accelerating the Understanding of
+ * Life's Code through Better Algorithms and Hardware Design" (ETH Zurich,
+ * 2018, rev. 2019):
+ *   - the (2E+1)-diagonal neighbourhood map of pairwise mismatches
+ *     (Ch. 6, Eq. 6.1; vacant cells are mismatches, Ch. 6 Discussion),
+ *   - the SneakySnake decider on the unweighted neighbourhood maze
+ *     (Ch. 8, Eq. 8.2, §8.4.2),
+ *   - the GateKeeper decider: Hamming fast path, amending of short zero
+ *     streaks, AND of the 2E+1 masks and popcount (Ch. 5, §5.2.1-§5.2.3),
+ *   - verification of accepted pairs by banded Levenshtein distance
+ *     (Ch. 2 "Accelerating Read Alignment": Ukkonen's band of 2E+1
+ *     diagonals), here a bit-vector (Myers/Hyyrö style) kernel.
+ *
+ * Conventions shared by every entry point:
+ *   - Array arguments are DEVICE pointers owned by the caller unless a
+ *     parameter says "host".  Calls are asynchronous on the context's
+ *     stream; pf_sync() joins them.  The library owns only its context,
+ *     its scratch memory and its tuning table.
+ *   - The grid column is the reference position i; the diagonal offset
+ *     d in [-E, E] indexes the read: cell (i, d) compares ref[i] with
+ *     read[i+d].  Cells with i+d outside the read are mismatches.
+ *   - 'N' (either case) never matches, not even another 'N'.
+ *   - A read and its reference segment have the same length len >= 0.
+ *     len = 0 gives accept = 1, count = 0, dist = 0.
+ *   - 0 <= E <= PF_MAX_E.  Counts saturate at E + 1; accept = (count <= E).
+ *   - Errors a host check can see (null pointers, negative sizes, E_max
+ *     out of range) return PF_EINVAL at once and launch nothing.  Errors
+ *     found on the device (a per-pair E above E_max or a negative length; a
+ *     byte that is not A/C/G/T/N) mark that pair's outputs (count = -1,
+ *     accept = 0, dist = -1) or pack the byte as N, and are reported by the
+ *     next pf_sync() as PF_EINVAL (PF_EDATA for bytes).  Errors are sticky
+ *     per context until pf_last_error() is read.  No exception crosses
+ *     this interface.
+ */
+#ifndef PF_H
+#define PF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PF_MAX_E 31
+
+#if defined(__GNUC__)
+#define PF_API __attribute__((visibility("default")))
+#else
+#define PF_API
+#endif
+
+typedef struct pf_ctx pf_ctx;
+
+typedef enum {
+    PF_OK = 0,
+    PF_EINVAL = 1,      /* bad argument */
+    PF_ENOMEM = 2,      /* device or pinned allocation failed */
+    PF_ECUDA = 3,       /* a CUDA runtime call failed */
+    PF_ETIMEOUT = 4,    /* a bounded wait ran out */
+    PF_EBUSY = 5,       /* serving loop not in the needed state */
+    PF_ECANCELLED = 6,  /* request cancelled */
+    PF_EDATA = 7        /* input bytes outside A/C/G/T/N (packed as N) */
+} pf_status;
+
+/* Decider mask.  With both bits set the two deciders share one pass over
+ * the map; their outputs occupy two slots: [0, n) SneakySnake and
+ * [n, 2n) GateKeeper. */
+enum { PF_SNEAKYSNAKE = 1u, PF_GATEKEEPER = 2u };
+
+typedef struct {
+    int device;         /* CUDA device ordinal */
+    void *stream;       /* cudaStream_t the context launches on; NULL = the
+                           per-thread default stream */
+    size_t hbm_budget;  /* bytes the serving loop may hold for admitted
+                           requests; 0 = a quarter of free device memory */
+    unsigned flags;     /* reserved, must be 0 */
+} pf_config;
+
+/* Packed sequences: three bit-planes of 32-bit words.  Base b of a
+ * sequence sets bit (b % 32) of word (b / 32) counted from the sequence's
+ * first word, in `lo` (low code bit), `hi` (high code bit) and `nmask`
+ * (1 for N).  Codes: A = 00, C = 01, G = 10, T = 11 (§5.2.3 prints A = 00
+ * and T = 11).  The unused tail of a sequence's last word is N.
+ * Sequence s starts at word word_off[s] (int64, device) or, when word_off
+ * is NULL, at word s * stride_words. */
+typedef struct {
+    const uint32_t *lo;
+    const uint32_t *hi;
+    const uint32_t *nmask;
+    const int64_t *word_off;
+    int64_t stride_words;
+} pf_seqs;
+
+/* Pair p is read sequence p of `read` against reference segment p of
+ * `ref` (the problem statement of §8.1: reference A, read B, both of
+ * length m). */
+typedef struct {
+    pf_seqs read;
+    pf_seqs ref;
+} pf_pairs;
+
+/* ---- context ----------------------------------------------------------- */
+
+/* Create a context on cfg->device.  *out receives an opaque handle owned by
+ * the library; release it with pf_destroy.  PF_EINVAL on a bad config,
+ * PF_ECUDA if the device cannot be used. */
+PF_API pf_status pf_create(pf_ctx **out, const pf_config *cfg);
+
+/* Wait for outstanding work, free everything the context owns. */
+PF_API pf_status pf_destroy(pf_ctx *ctx);
+
+/* Change the stream later calls are enqueued on (cudaStream_t). */
+PF_API pf_status pf_set_stream(pf_ctx *ctx, void *stream);
+
+/* Block until every call enqueued so far has finished; return the first
+ * error recorded since the last pf_last_error (device-side errors
+ * included). */
+PF_API pf_status pf_sync(pf_ctx *ctx);
+
+/* Message of the first recorded error (static or context-owned storage,
+ * valid until the next call on ctx); clears the sticky error. */
+PF_API const char *pf_last_error(pf_ctx *ctx);
+
+/* Name of a status code. */
+PF_API const char *pf_status_string(pf_status s);
+
+/* ---- a1: packing (§5.2.3 two-bit encoding, host Read Encoder of Ch. 4) --- */
+
+/* Host helper: word offsets for sequences with byte ranges
+ * [byte_off_host[s], byte_off_host[s+1]).  Writes nseq + 1 exclusive
+ * prefix sums of ceil(len/32) into word_off_host (host, may be NULL) and
+ * the total into *total_words. */
+PF_API pf_status pf_pack_layout(const int64_t *byte_off_host, int64_t nseq,
+                         int64_t *word_off_host, int64_t *total_words);
+
+/* Pack nseq ASCII sequences.  ascii: device bytes; byte_off, word_off:
+ * device int64[nseq+1] (sequence s occupies bytes [byte_off[s],
+ * byte_off[s+1]) and words [word_off[s], word_off[s+1]) of each plane);
+ * lo/hi/nmask: caller-allocated device planes of word_off[nseq] words.
+ * Bytes other than A/C/G/T/N (either case) pack as N and raise PF_EDATA
+ * at the next pf_sync. */
+PF_API pf_status pf_pack(pf_ctx *ctx, const uint8_t *ascii, const int64_t *byte_off,
+                  const int64_t *word_off, int64_t nseq,
+                  uint32_t *lo, uint32_t *hi, uint32_t *nmask);
+
+/* Same for nseq sequences of one length len stored back to back:
+ * sequence s is ascii[s*len, (s+1)*len) and occupies words
+ * [s*W, (s+1)*W) with W = ceil(len/32). */
+PF_API pf_status pf_pack_fixed(pf_ctx *ctx, const uint8_t *ascii, int64_t nseq, int len,
+                        uint32_t *lo, uint32_t *hi, uint32_t *nmask);
+
+/* ---- a2-a4, a7: filtering ----------------------------------------------- */
+
+/* Neighbourhood map + deciders for n pairs through the batch scheduler:
+ * pairs are grouped by threshold, each group runs the tuned mapping
+ * (threads per pair, work chunk) in one persistent launch.
+ *   deciders  PF_SNEAKYSNAKE, PF_GATEKEEPER or both (two output slots)
+ *   lens      device int32[n], pair lengths
+ *   E         device int16[n] per-pair thresholds, or NULL for E_max for
+ *             every pair
+ *   E_max     host int, 0..PF_MAX_E, upper bound of every E[p]
+ *   accept    device uint8[slots*n]
+ *   count     device int16[slots*n], saturated obstacle / edit counts */
+PF_API pf_status pf_filter(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs,
+                    const int32_t *lens, const int16_t *E, int E_max,
+                    uint8_t *accept, int16_t *count, int64_t n);
+
+/* The plain kernel: one thread per pair, one launch over all pairs, no
+ * scheduler.  Same arguments and results as pf_filter. */
+PF_API pf_status pf_filter_plain(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs,
+                          const int32_t *lens, const int16_t *E, int E_max,
+                          uint8_t *accept, int16_t *count, int64_t n);
+
+/* ---- a7: scheduler tuning --------------------------------------------------- */
+
+/* Kernel configurations of the batch scheduler.  Writes up to cap entries
+ * (lanes per pair, diagonal slots per lane, largest E served) into the
+ * host arrays (any may be NULL) and the number of configurations into
+ * *count. */
+PF_API pf_status pf_kernel_configs(int *tpp, int *dpt, int *ecap, int cap, int *count);
+
+/* Use configuration cfg and a work chunk of `chunk` pairs (1..65536) for
+ * threshold E under decider set `deciders` in later pf_filter calls.
+ * PF_EINVAL if cfg cannot serve E. */
+PF_API pf_status pf_tune_set(pf_ctx *ctx, unsigned deciders, int E, int cfg, int chunk);
+
+/* The configuration and chunk currently used for (deciders, E). */
+PF_API pf_status pf_tune_get(pf_ctx *ctx, unsigned deciders, int E, int *cfg, int *chunk);
+
+/* Autotuner: time every configuration that serves E, with work chunks of
+ * 64, 256 and 1024 pairs, on the n given pairs evaluated at threshold E
+ * (CUDA events on the context's stream, best of `reps` runs each), keep
+ * the fastest for (deciders, E) and report it (host outputs, may be NULL).
+ * Synchronises the stream.  Allocates and frees its own output buffers. */
+PF_API pf_status pf_tune(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs,
+                         const int32_t *lens, int E, int64_t n, int reps,
+                         int *best_cfg, int *best_chunk, float *best_ms);
+
+/* ---- a5: compaction ------------------------------------------------------ */
+
+/* Indices p (ascending) with flags[p] != 0, p < n, into idx (device
+ * int64[n]); their number into *n_out (device int64). */
+PF_API pf_status pf_compact(pf_ctx *ctx, const uint8_t *flags, int64_t n,
+                     int64_t *idx, int64_t *n_out);
+
+/* ---- a6: verification ---------------------------------------------------- */
+
+/* dist = min(Levenshtein(read, ref), E + 1) for the selected pairs, exact.
+ *   idx == NULL : pairs 0..n-1, dist[p] written for each.
+ *   idx != NULL : pairs idx[t] for t < *n_idx (device int64, <= n);
+ *                 dist[idx[t]] written, other entries untouched. */
+PF_API pf_status pf_verify(pf_ctx *ctx, const pf_pairs *pairs, const int32_t *lens,
+                    const int16_t *E, int E_max, const int64_t *idx,
+                    const int64_t *n_idx, int64_t n, int32_t *dist);
+
+/* Whole path for n pairs: filter (deciders as in pf_filter), compact the
+ * pairs the first selected decider accepts, verify them; dist[p] =
+ * min(ED, E+1) for those and E + 1 for every rejected pair. */
+PF_API pf_status pf_filter_verify(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs,
+                           const int32_t *lens, const int16_t *E, int E_max,
+                           uint8_t *accept, int16_t *count, int32_t *dist, int64_t n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PF_H */

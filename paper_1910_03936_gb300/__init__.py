@@ -1,0 +1,354 @@
+"""GB300-native pre-alignment filtering: neighbourhood map, SneakySnake and
+GateKeeper deciders, compaction and banded bit-vector verification, behind
+the C ABI of ``include/pf.h``.
+
+This module is argument marshalling only: every function below forwards
+torch tensors (device memory) to the function of the same name in
+``libpf.so`` and turns a non-OK status into :class:`PFError`.  There is no
+CPU fallback: every call raises when the library has not been built.
+"""
+import ctypes
+import os
+
+import torch
+
+from . import build as _build_mod
+
+__all__ = [
+    "PFError", "Seqs", "Pairs", "PF_SNEAKYSNAKE", "PF_GATEKEEPER", "PF_MAX_E",
+    "pf_create", "pf_destroy", "pf_set_stream", "pf_sync", "pf_last_error",
+    "pf_pack_layout", "pf_pack", "pf_pack_fixed", "pf_filter", "pf_filter_plain",
+    "pf_compact", "pf_verify", "pf_filter_verify", "library_path", "load", "pack_pairs",
+    "pf_kernel_configs", "pf_tune_set", "pf_tune_get", "pf_tune",
+]
+
+PF_SNEAKYSNAKE = 1
+PF_GATEKEEPER = 2
+PF_MAX_E = 31
+
+_STATUS = {0: "PF_OK", 1: "PF_EINVAL", 2: "PF_ENOMEM", 3: "PF_ECUDA", 4: "PF_ETIMEOUT",
+           5: "PF_EBUSY", 6: "PF_ECANCELLED", 7: "PF_EDATA"}
+
+
+class PFError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (_STATUS.get(status, status), message))
+        self.status = status
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("hbm_budget", ctypes.c_size_t), ("flags", ctypes.c_uint)]
+
+
+class _Seqs(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_void_p), ("hi", ctypes.c_void_p), ("nmask", ctypes.c_void_p),
+                ("word_off", ctypes.c_void_p), ("stride_words", ctypes.c_int64)]
+
+
+class _Pairs(ctypes.Structure):
+    _fields_ = [("read", _Seqs), ("ref", _Seqs)]
+
+
+_lib = None
+
+
+def library_path():
+    return _build_mod.LIB
+
+
+def load():
+    """Load ``libpf.so``; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise ImportError("libpf.so is not built (run paper_1910_03936_gb300.build.build())")
+    lib = ctypes.CDLL(path)
+    P, I, I64, U, S = (ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint,
+                       ctypes.c_int)
+    sig = {
+        "pf_create": [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(_Config)],
+        "pf_destroy": [P],
+        "pf_set_stream": [P, P],
+        "pf_sync": [P],
+        "pf_pack_layout": [P, I64, P, ctypes.POINTER(ctypes.c_int64)],
+        "pf_pack": [P, P, P, P, I64, P, P, P],
+        "pf_pack_fixed": [P, P, I64, I, P, P, P],
+        "pf_filter": [P, U, ctypes.POINTER(_Pairs), P, P, I, P, P, I64],
+        "pf_filter_plain": [P, U, ctypes.POINTER(_Pairs), P, P, I, P, P, I64],
+        "pf_compact": [P, P, I64, P, P],
+        "pf_verify": [P, ctypes.POINTER(_Pairs), P, P, I, P, P, I64, P],
+        "pf_filter_verify": [P, U, ctypes.POINTER(_Pairs), P, P, I, P, P, P, I64],
+        "pf_kernel_configs": [P, P, P, I, ctypes.POINTER(ctypes.c_int)],
+        "pf_tune_set": [P, U, I, I, I],
+        "pf_tune_get": [P, U, I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+        "pf_tune": [P, U, ctypes.POINTER(_Pairs), P, I, I64, I, ctypes.POINTER(ctypes.c_int),
+                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = S
+    lib.pf_last_error.argtypes = [P]
+    lib.pf_last_error.restype = ctypes.c_char_p
+    lib.pf_status_string.argtypes = [S]
+    lib.pf_status_string.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(status, ctx=None):
+    if status != 0:
+        msg = load().pf_last_error(ctx).decode() if ctx is not None else ""
+        raise PFError(status, msg)
+
+
+def _p(t):
+    """Device address of a tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _dt(t, dtype, name):
+    if t is not None and t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+
+
+class Seqs:
+    """Packed sequences: three int32 bit-plane tensors and either int64 word
+    offsets (n+1 entries) or a fixed stride in words."""
+
+    def __init__(self, lo, hi, nmask, word_off=None, stride_words=0):
+        for t, nm in ((lo, "lo"), (hi, "hi"), (nmask, "nmask")):
+            _dt(t, torch.int32, nm)
+        _dt(word_off, torch.int64, "word_off")
+        self.lo, self.hi, self.nmask = lo, hi, nmask
+        self.word_off, self.stride_words = word_off, int(stride_words)
+
+    def _c(self):
+        return _Seqs(self.lo.data_ptr(), self.hi.data_ptr(), self.nmask.data_ptr(),
+                     self.word_off.data_ptr() if self.word_off is not None else None,
+                     self.stride_words)
+
+    @staticmethod
+    def empty(total_words, device, word_off=None, stride_words=0):
+        mk = lambda: torch.empty(max(int(total_words), 1), dtype=torch.int32, device=device)
+        return Seqs(mk(), mk(), mk(), word_off, stride_words)
+
+
+class Pairs:
+    def __init__(self, read, ref):
+        self.read, self.ref = read, ref
+
+    def _c(self):
+        return _Pairs(self.read._c(), self.ref._c())
+
+
+class _Ctx:
+    """Owning handle of a pf_ctx."""
+
+    def __init__(self, handle, device):
+        self.handle, self.device = handle, device
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            try:
+                _lib.pf_destroy(self.handle)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def _cur_stream(ctx):
+    st = torch.cuda.current_stream(ctx.device).cuda_stream
+    _check(load().pf_set_stream(ctx.handle, ctypes.c_void_p(st)), ctx.handle)
+
+
+def pf_create(device=0, stream=None, hbm_budget=0):
+    lib = load()
+    cfg = _Config(device, stream if stream is not None
+                  else torch.cuda.current_stream(device).cuda_stream, hbm_budget, 0)
+    h = ctypes.c_void_p()
+    st = lib.pf_create(ctypes.byref(h), ctypes.byref(cfg))
+    if st != 0:
+        raise PFError(st, lib.pf_last_error(None).decode())
+    return _Ctx(h, device)
+
+
+def pf_destroy(ctx):
+    if ctx.handle:
+        st = load().pf_destroy(ctx.handle)
+        ctx.handle = None
+        _check(st)
+
+
+def pf_set_stream(ctx, stream):
+    _check(load().pf_set_stream(ctx.handle, ctypes.c_void_p(int(stream))), ctx.handle)
+
+
+def pf_sync(ctx):
+    _check(load().pf_sync(ctx.handle), ctx.handle)
+
+
+def pf_last_error(ctx):
+    return load().pf_last_error(ctx.handle).decode()
+
+
+def pf_pack_layout(byte_off):
+    """Host int64 byte offsets (numpy or list, nseq+1) -> (word_off numpy, total)."""
+    import numpy as np
+    bo = np.ascontiguousarray(byte_off, dtype=np.int64)
+    nseq = len(bo) - 1
+    wo = np.zeros(nseq + 1, dtype=np.int64)
+    total = ctypes.c_int64()
+    _check(load().pf_pack_layout(ctypes.c_void_p(bo.ctypes.data), nseq,
+                                 ctypes.c_void_p(wo.ctypes.data), ctypes.byref(total)))
+    return wo, int(total.value)
+
+
+def pf_pack(ctx, ascii, byte_off, word_off, out):
+    """Pack ragged ASCII (uint8 device tensor) into ``out`` (a Seqs)."""
+    _dt(ascii, torch.uint8, "ascii")
+    _dt(byte_off, torch.int64, "byte_off")
+    _dt(word_off, torch.int64, "word_off")
+    _cur_stream(ctx)
+    nseq = byte_off.numel() - 1
+    _check(load().pf_pack(ctx.handle, _p(ascii), _p(byte_off), _p(word_off), nseq,
+                          _p(out.lo), _p(out.hi), _p(out.nmask)), ctx.handle)
+
+
+def pf_pack_fixed(ctx, ascii, nseq, length, out):
+    _dt(ascii, torch.uint8, "ascii")
+    _cur_stream(ctx)
+    _check(load().pf_pack_fixed(ctx.handle, _p(ascii), int(nseq), int(length), _p(out.lo),
+                                _p(out.hi), _p(out.nmask)), ctx.handle)
+
+
+def _filter_call(fn, ctx, deciders, pairs, lens, E, E_max, accept, count, n):
+    _dt(lens, torch.int32, "lens")
+    _dt(E, torch.int16, "E")
+    _dt(accept, torch.uint8, "accept")
+    _dt(count, torch.int16, "count")
+    _cur_stream(ctx)
+    cp = pairs._c()
+    _check(fn(ctx.handle, int(deciders), ctypes.byref(cp), _p(lens), _p(E), int(E_max),
+              _p(accept), _p(count), int(n)), ctx.handle)
+
+
+def pf_filter(ctx, deciders, pairs, lens, E, E_max, accept, count, n=None):
+    n = lens.numel() if n is None else n
+    _filter_call(load().pf_filter, ctx, deciders, pairs, lens, E, E_max, accept, count, n)
+
+
+def pf_filter_plain(ctx, deciders, pairs, lens, E, E_max, accept, count, n=None):
+    n = lens.numel() if n is None else n
+    _filter_call(load().pf_filter_plain, ctx, deciders, pairs, lens, E, E_max, accept, count, n)
+
+
+def pf_compact(ctx, flags, idx, n_out, n=None):
+    _dt(flags, torch.uint8, "flags")
+    _dt(idx, torch.int64, "idx")
+    _dt(n_out, torch.int64, "n_out")
+    n = flags.numel() if n is None else n
+    _cur_stream(ctx)
+    _check(load().pf_compact(ctx.handle, _p(flags), int(n), _p(idx), _p(n_out)), ctx.handle)
+
+
+def pf_verify(ctx, pairs, lens, E, E_max, idx, n_idx, dist, n=None):
+    _dt(lens, torch.int32, "lens")
+    _dt(E, torch.int16, "E")
+    _dt(idx, torch.int64, "idx")
+    _dt(n_idx, torch.int64, "n_idx")
+    _dt(dist, torch.int32, "dist")
+    n = lens.numel() if n is None else n
+    _cur_stream(ctx)
+    cp = pairs._c()
+    _check(load().pf_verify(ctx.handle, ctypes.byref(cp), _p(lens), _p(E), int(E_max), _p(idx),
+                            _p(n_idx), int(n), _p(dist)), ctx.handle)
+
+
+def pf_filter_verify(ctx, deciders, pairs, lens, E, E_max, accept, count, dist, n=None):
+    _dt(lens, torch.int32, "lens")
+    _dt(E, torch.int16, "E")
+    _dt(accept, torch.uint8, "accept")
+    _dt(count, torch.int16, "count")
+    _dt(dist, torch.int32, "dist")
+    n = lens.numel() if n is None else n
+    _cur_stream(ctx)
+    cp = pairs._c()
+    _check(load().pf_filter_verify(ctx.handle, int(deciders), ctypes.byref(cp), _p(lens), _p(E),
+                                   int(E_max), _p(accept), _p(count), _p(dist), int(n)),
+           ctx.handle)
+
+
+def pack_pairs(ctx, reads, refs, length=None, byte_off=None):
+    """Pack device ASCII reads and refs (uint8 tensors) with pf_pack.
+
+    Fixed length: pass ``length`` (sequence s is bytes [s*length,
+    (s+1)*length)).  Ragged: pass ``byte_off`` as host int64 offsets
+    (numpy, n+1 entries) shared by reads and refs; word offsets come from
+    pf_pack_layout.  Returns a :class:`Pairs`.
+    """
+    dev = reads.device
+    if length is not None:
+        n = reads.numel() // length if length else 0
+        W = (length + 31) // 32
+        out = []
+        for src in (reads, refs):
+            s = Seqs.empty(n * W, dev, stride_words=W)
+            if n and length:
+                pf_pack_fixed(ctx, src, n, length, s)
+            out.append(s)
+        return Pairs(out[0], out[1])
+    import numpy as np
+    wo, total = pf_pack_layout(byte_off)
+    bo_d = torch.from_numpy(np.ascontiguousarray(byte_off, dtype=np.int64)).to(dev)
+    wo_d = torch.from_numpy(wo).to(dev)
+    out = []
+    for src in (reads, refs):
+        s = Seqs.empty(total, dev, word_off=wo_d)
+        pf_pack(ctx, src, bo_d, wo_d, s)
+        out.append(s)
+    return Pairs(out[0], out[1])
+
+
+def pf_kernel_configs():
+    """List of (tpp, dpt, ecap) of the batch scheduler's kernels."""
+    import numpy as np
+    cnt = ctypes.c_int()
+    _check(load().pf_kernel_configs(None, None, None, 0, ctypes.byref(cnt)))
+    a = [np.zeros(cnt.value, dtype=np.int32) for _ in range(3)]
+    _check(load().pf_kernel_configs(*[ctypes.c_void_p(x.ctypes.data) for x in a], cnt.value,
+                                    ctypes.byref(cnt)))
+    return [(int(a[0][i]), int(a[1][i]), int(a[2][i])) for i in range(cnt.value)]
+
+
+def pf_tune_set(ctx, deciders, E, cfg, chunk):
+    _check(load().pf_tune_set(ctx.handle, int(deciders), int(E), int(cfg), int(chunk)), ctx.handle)
+
+
+def pf_tune_get(ctx, deciders, E):
+    c, k = ctypes.c_int(), ctypes.c_int()
+    _check(load().pf_tune_get(ctx.handle, int(deciders), int(E), ctypes.byref(c), ctypes.byref(k)),
+           ctx.handle)
+    return c.value, k.value
+
+
+def pf_tune(ctx, deciders, pairs, lens, E, n=None, reps=3):
+    """Autotune (deciders, E) on these pairs; returns (cfg, chunk, ms)."""
+    _dt(lens, torch.int32, "lens")
+    n = lens.numel() if n is None else n
+    _cur_stream(ctx)
+    cp = pairs._c()
+    c, k, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+    _check(load().pf_tune(ctx.handle, int(deciders), ctypes.byref(cp), _p(lens), int(E), int(n),
+                          int(reps), ctypes.byref(c), ctypes.byref(k), ctypes.byref(ms)),
+           ctx.handle)
+    return c.value, k.value, ms.value

@@ -1,0 +1,648 @@
+// C-ABI of the library: context, argument checks, the batch scheduler
+// (binning by threshold, tuned kernel per bin, concurrent persistent
+// launches) and the whole-path call.  Declarations and contracts: pf.h.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "pf_ctx.h"
+#include "pf_kernels.h"
+
+using namespace pf;
+
+namespace pf {
+
+// ---------------------------------------------------------------------------
+// binning kernels: group pair indices by the configuration of their E
+
+struct BinTable {
+    int cfg_of_E[PF_MAX_E + 1];
+};
+
+__global__ void bin_init_kernel(int64_t *bin_start, unsigned long long *work,
+                                unsigned long long *hist, int nb, int single_cfg, int64_t n) {
+    const int i = threadIdx.x;
+    if (i <= nb) bin_start[i] = (single_cfg >= 0) ? (i <= single_cfg ? 0 : n) : 0;
+    if (i < nb) {
+        work[i] = 0ull;
+        hist[i] = 0ull;
+    }
+}
+
+__device__ __forceinline__ int bin_key(const int16_t *E, int64_t p, int E_max, const BinTable &t) {
+    int e = __ldg(E + p);
+    e = e < 0 ? 0 : (e > E_max ? E_max : e);
+    return t.cfg_of_E[e];
+}
+
+__global__ void __launch_bounds__(256)
+bin_hist_kernel(const int16_t *E, int64_t n, int E_max, BinTable t, unsigned long long *hist) {
+    __shared__ unsigned cnt[kNumBatchCfgs];
+    for (int i = threadIdx.x; i < kNumBatchCfgs; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[bin_key(E, p, E_max, t)], 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kNumBatchCfgs; i += blockDim.x)
+        if (cnt[i]) atomicAdd(&hist[i], (unsigned long long)cnt[i]);
+}
+
+__global__ void bin_scan_kernel(const unsigned long long *hist, int64_t *bin_start,
+                                unsigned long long *cursor) {
+    if (threadIdx.x != 0) return;
+    int64_t acc = 0;
+    for (int i = 0; i < kNumBatchCfgs; ++i) {
+        bin_start[i] = acc;
+        cursor[i] = (unsigned long long)acc;
+        acc += (int64_t)hist[i];
+    }
+    bin_start[kNumBatchCfgs] = acc;
+}
+
+// Each block claims room for its pairs per bin with one atomic per bin and
+// places its pairs there (order inside a block's share is arbitrary; every
+// pair keeps its own index, so results do not depend on it).
+__global__ void __launch_bounds__(256)
+bin_scatter_kernel(const int16_t *E, int64_t n, int E_max, BinTable t,
+                   unsigned long long *cursor, int64_t *order) {
+    __shared__ unsigned cnt[kNumBatchCfgs];
+    __shared__ unsigned long long base[kNumBatchCfgs];
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int i = threadIdx.x; i < kNumBatchCfgs; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    int key = -1;
+    unsigned rank = 0;
+    if (p < n) {
+        key = bin_key(E, p, E_max, t);
+        rank = atomicAdd(&cnt[key], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kNumBatchCfgs; i += blockDim.x)
+        base[i] = cnt[i] ? atomicAdd(&cursor[i], (unsigned long long)cnt[i]) : 0ull;
+    __syncthreads();
+    if (p < n) order[base[key] + rank] = p;
+}
+
+// dist[p] = E_p + 1 for pairs the filter rejected (verification skips them)
+__global__ void __launch_bounds__(256)
+dist_fill_rejected_kernel(const uint8_t *accept, const int16_t *E, int E_max, int64_t n,
+                          int32_t *dist) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        if (!accept[p]) {
+            const int e = E ? (int)E[p] : E_max;
+            dist[p] = (e < 0 || e > E_max) ? -1 : e + 1;
+        }
+    }
+}
+
+}  // namespace pf
+
+// ---------------------------------------------------------------------------
+// context helpers
+
+static thread_local std::string g_tls_msg;
+
+void pf_serve_teardown(pf_ctx *) {}
+
+pf_status pf_ctx::fail(pf_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    std::lock_guard<std::mutex> lk(mu);
+    if (sticky == PF_OK) {
+        sticky = s;
+        msg = buf;
+    }
+    return s;
+}
+
+pf_status pf_ctx::cuda(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return PF_OK;
+    return fail(PF_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+pf_status pf_ctx::ensure_scratch(size_t bytes) {
+    if (bytes <= scratch_bytes) return PF_OK;
+    if (scratch) {
+        cudaStreamSynchronize(stream);
+        cudaFree(scratch);
+        scratch = nullptr;
+        scratch_bytes = 0;
+    }
+    size_t want = std::max(bytes, scratch_bytes * 3 / 2);
+    if (cudaMalloc(&scratch, want) != cudaSuccess) {
+        cudaGetLastError();
+        if (cudaMalloc(&scratch, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            scratch = nullptr;
+            return fail(PF_ENOMEM, "scratch allocation of %zu bytes failed", bytes);
+        }
+        want = bytes;
+    }
+    scratch_bytes = want;
+    return PF_OK;
+}
+
+// Carve the scratch block: returns pointers for n pairs.
+pf_status pf_ctx::scratch_layout(int64_t n, Scratch *s) {
+    auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+    const size_t nn = (size_t)std::max<int64_t>(n, 1);
+    size_t off = 0;
+    const size_t o_order = off; off += up(nn * sizeof(int64_t));
+    const size_t o_idx = off;   off += up(nn * sizeof(int64_t));
+    const size_t o_nidx = off;  off += up(sizeof(int64_t));
+    const size_t o_tiles = off; off += up((size_t)compact_tiles((int64_t)nn) * sizeof(int64_t));
+    const size_t o_bins = off;  off += up((kNumBatchCfgs + 1) * sizeof(int64_t));
+    const size_t o_work = off;  off += up(kNumBatchCfgs * sizeof(unsigned long long));
+    const size_t o_hist = off;  off += up(kNumBatchCfgs * sizeof(unsigned long long));
+    const size_t o_cur = off;   off += up(kNumBatchCfgs * sizeof(unsigned long long));
+    pf_status st = ensure_scratch(off);
+    if (st != PF_OK) return st;
+    char *b = static_cast<char *>(scratch);
+    s->order = reinterpret_cast<int64_t *>(b + o_order);
+    s->idx = reinterpret_cast<int64_t *>(b + o_idx);
+    s->n_idx = reinterpret_cast<int64_t *>(b + o_nidx);
+    s->tiles = reinterpret_cast<int64_t *>(b + o_tiles);
+    s->bin_start = reinterpret_cast<int64_t *>(b + o_bins);
+    s->work = reinterpret_cast<unsigned long long *>(b + o_work);
+    s->hist = reinterpret_cast<unsigned long long *>(b + o_hist);
+    s->cursor = reinterpret_cast<unsigned long long *>(b + o_cur);
+    return PF_OK;
+}
+
+int pf_ctx::grid_for(int dec, int cfg) {
+    int &g = grid_cache[dec][cfg];
+    if (g == 0) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, filter_batched_fn(dec, cfg), 256, 0);
+        g = std::max(1, per_sm) * sms;
+    }
+    return g;
+}
+
+// Default configuration for threshold E before any tuning: the smallest
+// capacity that fits, one lane per pair up to E = 7, then wider groups.
+int pf::pf_default_cfg(int E) {
+    int want_tpp = E <= 7 ? 1 : (E <= 15 ? 4 : 8);
+    int best = -1;
+    for (int c = 0; c < kNumBatchCfgs; ++c) {
+        if (kBatchCfgs[c].ecap < E) continue;
+        if (best < 0 || kBatchCfgs[c].ecap < kBatchCfgs[best].ecap ||
+            (kBatchCfgs[c].ecap == kBatchCfgs[best].ecap && kBatchCfgs[c].tpp == want_tpp))
+            best = c;
+    }
+    return best;
+}
+
+void pf_ctx::reset_tuning() {
+    for (int d = 0; d < 4; ++d)
+        for (int e = 0; e <= PF_MAX_E; ++e) {
+            tune_cfg[d][e] = pf_default_cfg(e);
+            tune_chunk[d][e] = 256;
+        }
+}
+
+// ---------------------------------------------------------------------------
+// argument checks
+
+static bool seqs_ok(const pf_seqs &s) {
+    return s.lo && s.hi && s.nmask && (s.word_off || s.stride_words >= 0);
+}
+
+static PairsView to_view(const pf_pairs *p) {
+    PairsView v;
+    v.read = SeqView{p->read.lo, p->read.hi, p->read.nmask, p->read.word_off, p->read.stride_words};
+    v.ref = SeqView{p->ref.lo, p->ref.hi, p->ref.nmask, p->ref.word_off, p->ref.stride_words};
+    return v;
+}
+
+static pf_status check_filter_args(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs,
+                                   const int32_t *lens, int E_max, uint8_t *accept,
+                                   int16_t *count, int64_t n) {
+    if (!ctx) return PF_EINVAL;
+    if (n < 0) return ctx->fail(PF_EINVAL, "n = %lld < 0", (long long)n);
+    if ((deciders & 3u) == 0 || (deciders & ~3u))
+        return ctx->fail(PF_EINVAL, "deciders must be PF_SNEAKYSNAKE, PF_GATEKEEPER or both");
+    if (E_max < 0 || E_max > PF_MAX_E)
+        return ctx->fail(PF_EINVAL, "E_max = %d outside [0, %d]", E_max, PF_MAX_E);
+    if (n == 0) return PF_OK;
+    if (!pairs || !seqs_ok(pairs->read) || !seqs_ok(pairs->ref) || !lens || !accept || !count)
+        return ctx->fail(PF_EINVAL, "null pointer argument");
+    return PF_OK;
+}
+
+static FilterArgs make_filter_args(pf_ctx *ctx, const pf_pairs *pairs, const int32_t *lens,
+                                   const int16_t *E, int E_max, uint8_t *accept, int16_t *count,
+                                   int64_t n) {
+    FilterArgs a;
+    a.pairs = to_view(pairs);
+    a.lens = lens;
+    a.E = E;
+    a.E_max = E_max;
+    a.accept = accept;
+    a.count = count;
+    a.n = n;
+    a.err = ctx->d_err;
+    return a;
+}
+
+// ---------------------------------------------------------------------------
+// scheduler
+
+pf_status pf_ctx::run_batched(unsigned dec, const FilterArgs &a, const Scratch &s) {
+    BatchArgs b;
+    b.f = a;
+    b.bin_start = s.bin_start;
+    b.bin_cfg = nullptr;
+    b.nbins = kNumBatchCfgs;
+    b.work = s.work;
+    b.chunk_start = nullptr;
+    std::vector<int> used;
+    int single = -1;
+    if (!a.E) {
+        single = tune_cfg[dec][a.E_max];
+        used.push_back(single);
+        b.order = nullptr;
+    } else {
+        b.order = s.order;
+        for (int e = 0; e <= a.E_max; ++e) {
+            const int c = tune_cfg[dec][e];
+            if (std::find(used.begin(), used.end(), c) == used.end()) used.push_back(c);
+        }
+        if (used.size() == 1) {
+            single = used[0];
+            b.order = nullptr;
+        }
+    }
+    bin_init_kernel<<<1, 32, 0, stream>>>(s.bin_start, s.work, s.hist, kNumBatchCfgs, single,
+                                          a.n);
+    if (single < 0) {
+        BinTable t;
+        for (int e = 0; e <= PF_MAX_E; ++e) t.cfg_of_E[e] = tune_cfg[dec][std::min(e, a.E_max)];
+        int64_t hb = std::min<int64_t>((a.n + 255) / 256, (int64_t)sms * 8);
+        bin_hist_kernel<<<(unsigned)std::max<int64_t>(hb, 1), 256, 0, stream>>>(a.E, a.n, a.E_max,
+                                                                               t, s.hist);
+        bin_scan_kernel<<<1, 32, 0, stream>>>(s.hist, s.bin_start, s.cursor);
+        bin_scatter_kernel<<<(unsigned)((a.n + 255) / 256), 256, 0, stream>>>(
+            a.E, a.n, a.E_max, t, s.cursor, s.order);
+    }
+    pf_status st = cuda(cudaGetLastError(), "binning launch");
+    if (st != PF_OK) return st;
+
+    if (used.size() == 1) {
+        const int c = used[0];
+        b.chunk = tune_chunk[dec][a.E_max];
+        const int64_t items = (a.n + b.chunk - 1) / b.chunk;
+        const int grid = (int)std::min<int64_t>(grid_for(dec, c), std::max<int64_t>(1, (items + 7) / 8));
+        return cuda(launch_filter_batched(dec, c, grid, b, c, stream), "filter launch");
+    }
+    // several configurations: one persistent launch each, concurrently
+    cudaEventRecord(ev_fork, stream);
+    for (size_t i = 0; i < used.size(); ++i) {
+        cudaStream_t side = side_streams[i % kSideStreams];
+        cudaStreamWaitEvent(side, ev_fork, 0);
+        const int c = used[i];
+        BatchArgs bi = b;
+        bi.chunk = 256;
+        for (int e = 0; e <= a.E_max; ++e)
+            if (tune_cfg[dec][e] == c) bi.chunk = tune_chunk[dec][e];
+        const int grid = grid_for(dec, c);
+        st = cuda(launch_filter_batched(dec, c, grid, bi, c, side), "filter launch");
+        if (st != PF_OK) return st;
+    }
+    for (int i = 0; i < kSideStreams && i < (int)used.size(); ++i) {
+        cudaEventRecord(ev_join[i], side_streams[i]);
+        cudaStreamWaitEvent(stream, ev_join[i], 0);
+    }
+    return cuda(cudaGetLastError(), "filter launch");
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+
+extern "C" {
+
+const char *pf_status_string(pf_status s) {
+    switch (s) {
+        case PF_OK: return "PF_OK";
+        case PF_EINVAL: return "PF_EINVAL";
+        case PF_ENOMEM: return "PF_ENOMEM";
+        case PF_ECUDA: return "PF_ECUDA";
+        case PF_ETIMEOUT: return "PF_ETIMEOUT";
+        case PF_EBUSY: return "PF_EBUSY";
+        case PF_ECANCELLED: return "PF_ECANCELLED";
+        case PF_EDATA: return "PF_EDATA";
+    }
+    return "PF_?";
+}
+
+pf_status pf_create(pf_ctx **out, const pf_config *cfg) {
+    if (!out || !cfg || cfg->flags != 0) return PF_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
+        cudaGetLastError();
+        g_tls_msg = "no such CUDA device";
+        return PF_ECUDA;
+    }
+    if (cudaSetDevice(cfg->device) != cudaSuccess) return PF_ECUDA;
+    pf_ctx *c = new pf_ctx();
+    c->device = cfg->device;
+    c->stream = static_cast<cudaStream_t>(cfg->stream);
+    if (!c->stream) c->stream = cudaStreamPerThread;
+    c->hbm_budget = cfg->hbm_budget;
+    cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, cfg->device);
+    bool ok = cudaMalloc(&c->d_err, sizeof(unsigned)) == cudaSuccess &&
+              cudaMemset(c->d_err, 0, sizeof(unsigned)) == cudaSuccess &&
+              cudaMallocHost(&c->h_err, sizeof(unsigned)) == cudaSuccess &&
+              cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; ok && i < kSideStreams; ++i)
+        ok = cudaStreamCreateWithFlags(&c->side_streams[i], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&c->ev_join[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        pf_destroy(c);
+        return PF_ECUDA;
+    }
+    *c->h_err = 0;
+    c->reset_tuning();
+    *out = c;
+    return PF_OK;
+}
+
+pf_status pf_destroy(pf_ctx *ctx) {
+    if (!ctx) return PF_EINVAL;
+    cudaSetDevice(ctx->device);
+    pf_serve_teardown(ctx);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->scratch) cudaFree(ctx->scratch);
+    if (ctx->d_err) cudaFree(ctx->d_err);
+    if (ctx->h_err) cudaFreeHost(ctx->h_err);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    for (int i = 0; i < kSideStreams; ++i) {
+        if (ctx->side_streams[i]) cudaStreamDestroy(ctx->side_streams[i]);
+        if (ctx->ev_join[i]) cudaEventDestroy(ctx->ev_join[i]);
+    }
+    delete ctx;
+    return PF_OK;
+}
+
+pf_status pf_set_stream(pf_ctx *ctx, void *stream) {
+    if (!ctx) return PF_EINVAL;
+    ctx->stream = stream ? static_cast<cudaStream_t>(stream) : cudaStreamPerThread;
+    return PF_OK;
+}
+
+pf_status pf_sync(pf_ctx *ctx) {
+    if (!ctx) return PF_EINVAL;
+    cudaSetDevice(ctx->device);
+    pf_status st = ctx->cuda(cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(unsigned),
+                                             cudaMemcpyDeviceToHost, ctx->stream),
+                             "error word copy");
+    if (st == PF_OK) st = ctx->cuda(cudaStreamSynchronize(ctx->stream), "stream sync");
+    if (st == PF_OK && *ctx->h_err) {
+        const unsigned e = *ctx->h_err;
+        *ctx->h_err = 0;
+        cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream);
+        cudaStreamSynchronize(ctx->stream);
+        if (e & ERR_PAIR_ARGS)
+            ctx->fail(PF_EINVAL, "a pair had a negative length or E outside [0, E_max]");
+        else if (e & ERR_TIMEOUT)
+            ctx->fail(PF_ETIMEOUT, "a bounded device wait ran out");
+        else if (e & ERR_BYTES)
+            ctx->fail(PF_EDATA, "input bytes other than A/C/G/T/N were packed as N");
+    }
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    return ctx->sticky;
+}
+
+const char *pf_last_error(pf_ctx *ctx) {
+    if (!ctx) return g_tls_msg.empty() ? "no context" : g_tls_msg.c_str();
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->last_msg = ctx->sticky == PF_OK ? std::string("no error") : ctx->msg;
+    ctx->sticky = PF_OK;
+    ctx->msg.clear();
+    return ctx->last_msg.c_str();
+}
+
+pf_status pf_pack_layout(const int64_t *byte_off_host, int64_t nseq, int64_t *word_off_host,
+                         int64_t *total_words) {
+    if (!byte_off_host || nseq < 0 || !total_words) return PF_EINVAL;
+    int64_t acc = 0;
+    for (int64_t s = 0; s < nseq; ++s) {
+        const int64_t len = byte_off_host[s + 1] - byte_off_host[s];
+        if (len < 0) return PF_EINVAL;
+        if (word_off_host) word_off_host[s] = acc;
+        acc += (len + 31) / 32;
+    }
+    if (word_off_host) word_off_host[nseq] = acc;
+    *total_words = acc;
+    return PF_OK;
+}
+
+pf_status pf_pack(pf_ctx *ctx, const uint8_t *ascii, const int64_t *byte_off,
+                  const int64_t *word_off, int64_t nseq, uint32_t *lo, uint32_t *hi,
+                  uint32_t *nmask) {
+    if (!ctx) return PF_EINVAL;
+    if (nseq < 0) return ctx->fail(PF_EINVAL, "nseq < 0");
+    if (nseq == 0) return PF_OK;
+    if (!ascii || !byte_off || !word_off || !lo || !hi || !nmask)
+        return ctx->fail(PF_EINVAL, "null pointer argument");
+    cudaSetDevice(ctx->device);
+    return ctx->cuda(launch_pack_ragged(ascii, byte_off, word_off, nseq, lo, hi, nmask,
+                                        ctx->d_err, ctx->stream),
+                     "pack launch");
+}
+
+pf_status pf_pack_fixed(pf_ctx *ctx, const uint8_t *ascii, int64_t nseq, int len, uint32_t *lo,
+                        uint32_t *hi, uint32_t *nmask) {
+    if (!ctx) return PF_EINVAL;
+    if (nseq < 0 || len < 0) return ctx->fail(PF_EINVAL, "nseq or len < 0");
+    if (nseq == 0 || len == 0) return PF_OK;
+    if (!ascii || !lo || !hi || !nmask) return ctx->fail(PF_EINVAL, "null pointer argument");
+    cudaSetDevice(ctx->device);
+    return ctx->cuda(launch_pack_fixed(ascii, nseq, len, lo, hi, nmask, ctx->d_err, ctx->sms,
+                                       ctx->stream),
+                     "pack launch");
+}
+
+pf_status pf_filter_plain(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs,
+                          const int32_t *lens, const int16_t *E, int E_max, uint8_t *accept,
+                          int16_t *count, int64_t n) {
+    pf_status st = check_filter_args(ctx, deciders, pairs, lens, E_max, accept, count, n);
+    if (st != PF_OK || n == 0) return st;
+    cudaSetDevice(ctx->device);
+    int pi = 0;
+    while (pi < kNumPlain && kPlainDpt[pi] - 1 < E_max) ++pi;
+    const FilterArgs a = make_filter_args(ctx, pairs, lens, E, E_max, accept, count, n);
+    return ctx->cuda(launch_filter_plain((int)deciders, pi, a, ctx->stream), "filter launch");
+}
+
+pf_status pf_filter(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs, const int32_t *lens,
+                    const int16_t *E, int E_max, uint8_t *accept, int16_t *count, int64_t n) {
+    pf_status st = check_filter_args(ctx, deciders, pairs, lens, E_max, accept, count, n);
+    if (st != PF_OK || n == 0) return st;
+    cudaSetDevice(ctx->device);
+    Scratch s;
+    st = ctx->scratch_layout(n, &s);
+    if (st != PF_OK) return st;
+    const FilterArgs a = make_filter_args(ctx, pairs, lens, E, E_max, accept, count, n);
+    return ctx->run_batched(deciders, a, s);
+}
+
+pf_status pf_compact(pf_ctx *ctx, const uint8_t *flags, int64_t n, int64_t *idx,
+                     int64_t *n_out) {
+    if (!ctx) return PF_EINVAL;
+    if (n < 0) return ctx->fail(PF_EINVAL, "n < 0");
+    if (!n_out || (n > 0 && (!flags || !idx))) return ctx->fail(PF_EINVAL, "null pointer argument");
+    cudaSetDevice(ctx->device);
+    Scratch s;
+    pf_status st = ctx->scratch_layout(n, &s);
+    if (st != PF_OK) return st;
+    return ctx->cuda(launch_compact(flags, n, idx, n_out, s.tiles, ctx->stream), "compact launch");
+}
+
+pf_status pf_verify(pf_ctx *ctx, const pf_pairs *pairs, const int32_t *lens, const int16_t *E,
+                    int E_max, const int64_t *idx, const int64_t *n_idx, int64_t n,
+                    int32_t *dist) {
+    if (!ctx) return PF_EINVAL;
+    if (n < 0) return ctx->fail(PF_EINVAL, "n < 0");
+    if (E_max < 0 || E_max > PF_MAX_E)
+        return ctx->fail(PF_EINVAL, "E_max = %d outside [0, %d]", E_max, PF_MAX_E);
+    if (n == 0) return PF_OK;
+    if (!pairs || !seqs_ok(pairs->read) || !seqs_ok(pairs->ref) || !lens || !dist ||
+        (idx && !n_idx))
+        return ctx->fail(PF_EINVAL, "null pointer argument");
+    cudaSetDevice(ctx->device);
+    return ctx->cuda(launch_verify(to_view(pairs), lens, E, E_max, idx, n_idx, n, dist,
+                                   ctx->d_err, ctx->sms, ctx->stream),
+                     "verify launch");
+}
+
+pf_status pf_filter_verify(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs,
+                           const int32_t *lens, const int16_t *E, int E_max, uint8_t *accept,
+                           int16_t *count, int32_t *dist, int64_t n) {
+    pf_status st = check_filter_args(ctx, deciders, pairs, lens, E_max, accept, count, n);
+    if (st != PF_OK || n == 0) return st;
+    if (!dist) return ctx->fail(PF_EINVAL, "null pointer argument");
+    cudaSetDevice(ctx->device);
+    Scratch s;
+    st = ctx->scratch_layout(n, &s);
+    if (st != PF_OK) return st;
+    const FilterArgs a = make_filter_args(ctx, pairs, lens, E, E_max, accept, count, n);
+    st = ctx->run_batched(deciders, a, s);
+    if (st != PF_OK) return st;
+    // the first selected decider's accept flags choose the pairs to verify
+    st = ctx->cuda(launch_compact(accept, n, s.idx, s.n_idx, s.tiles, ctx->stream),
+                   "compact launch");
+    if (st != PF_OK) return st;
+    const int64_t fb = std::min<int64_t>((n + 255) / 256, (int64_t)ctx->sms * 16);
+    dist_fill_rejected_kernel<<<(unsigned)fb, 256, 0, ctx->stream>>>(accept, E, E_max, n, dist);
+    st = ctx->cuda(cudaGetLastError(), "fill launch");
+    if (st != PF_OK) return st;
+    return ctx->cuda(launch_verify(to_view(pairs), lens, E, E_max, s.idx, s.n_idx, n, dist,
+                                   ctx->d_err, ctx->sms, ctx->stream),
+                     "verify launch");
+}
+
+pf_status pf_kernel_configs(int *tpp, int *dpt, int *ecap, int cap, int *count) {
+    if (!count || cap < 0) return PF_EINVAL;
+    for (int c = 0; c < kNumBatchCfgs && c < cap; ++c) {
+        if (tpp) tpp[c] = kBatchCfgs[c].tpp;
+        if (dpt) dpt[c] = kBatchCfgs[c].dpt;
+        if (ecap) ecap[c] = kBatchCfgs[c].ecap;
+    }
+    *count = kNumBatchCfgs;
+    return PF_OK;
+}
+
+pf_status pf_tune_set(pf_ctx *ctx, unsigned deciders, int E, int cfg, int chunk) {
+    if (!ctx) return PF_EINVAL;
+    if ((deciders & 3u) == 0 || (deciders & ~3u) || E < 0 || E > PF_MAX_E || cfg < 0 ||
+        cfg >= kNumBatchCfgs || kBatchCfgs[cfg].ecap < E || chunk < 1 || chunk > 65536)
+        return ctx->fail(PF_EINVAL, "pf_tune_set: bad deciders/E/cfg/chunk");
+    ctx->tune_cfg[deciders][E] = cfg;
+    ctx->tune_chunk[deciders][E] = chunk;
+    return PF_OK;
+}
+
+pf_status pf_tune_get(pf_ctx *ctx, unsigned deciders, int E, int *cfg, int *chunk) {
+    if (!ctx) return PF_EINVAL;
+    if ((deciders & 3u) == 0 || (deciders & ~3u) || E < 0 || E > PF_MAX_E)
+        return ctx->fail(PF_EINVAL, "pf_tune_get: bad deciders/E");
+    if (cfg) *cfg = ctx->tune_cfg[deciders][E];
+    if (chunk) *chunk = ctx->tune_chunk[deciders][E];
+    return PF_OK;
+}
+
+pf_status pf_tune(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs, const int32_t *lens,
+                  int E, int64_t n, int reps, int *best_cfg, int *best_chunk, float *best_ms) {
+    if (!ctx) return PF_EINVAL;
+    if (n <= 0 || reps <= 0 || E < 0 || E > PF_MAX_E)
+        return ctx->fail(PF_EINVAL, "pf_tune: bad n/reps/E");
+    pf_status st = check_filter_args(ctx, deciders, pairs, lens, E, reinterpret_cast<uint8_t *>(1),
+                                     reinterpret_cast<int16_t *>(2), n);
+    if (st != PF_OK) return st;
+    cudaSetDevice(ctx->device);
+    const int slots = (deciders == 3u) ? 2 : 1;
+    uint8_t *acc = nullptr;
+    int16_t *cnt = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaMalloc(&acc, (size_t)slots * n) != cudaSuccess ||
+        cudaMalloc(&cnt, (size_t)slots * n * sizeof(int16_t)) != cudaSuccess) {
+        cudaGetLastError();
+        if (acc) cudaFree(acc);
+        return ctx->fail(PF_ENOMEM, "pf_tune: output buffers");
+    }
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    Scratch s;
+    st = ctx->scratch_layout(n, &s);
+    const int keep_cfg = ctx->tune_cfg[deciders][E], keep_chunk = ctx->tune_chunk[deciders][E];
+    int bc = keep_cfg, bk = keep_chunk;
+    float bms = 1e30f;
+    static const int chunks[] = {64, 256, 1024};
+    for (int c = 0; st == PF_OK && c < kNumBatchCfgs; ++c) {
+        if (kBatchCfgs[c].ecap < E) continue;
+        for (int k : chunks) {
+            ctx->tune_cfg[deciders][E] = c;
+            ctx->tune_chunk[deciders][E] = k;
+            const FilterArgs a = make_filter_args(ctx, pairs, lens, nullptr, E, acc, cnt, n);
+            float best = 1e30f;
+            for (int r = 0; r <= reps && st == PF_OK; ++r) {  // first run warms up
+                cudaEventRecord(e0, ctx->stream);
+                st = ctx->run_batched(deciders, a, s);
+                cudaEventRecord(e1, ctx->stream);
+                if (st == PF_OK) st = ctx->cuda(cudaEventSynchronize(e1), "tune sync");
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (r > 0 && ms < best) best = ms;
+            }
+            if (best < bms) {
+                bms = best;
+                bc = c;
+                bk = k;
+            }
+        }
+    }
+    ctx->tune_cfg[deciders][E] = (st == PF_OK) ? bc : keep_cfg;
+    ctx->tune_chunk[deciders][E] = (st == PF_OK) ? bk : keep_chunk;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(acc);
+    cudaFree(cnt);
+    if (st != PF_OK) return st;
+    if (best_cfg) *best_cfg = bc;
+    if (best_chunk) *best_chunk = bk;
+    if (best_ms) *best_ms = bms;
+    return PF_OK;
+}
+
+}  // extern "C"

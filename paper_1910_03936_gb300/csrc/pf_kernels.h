@@ -1,0 +1,48 @@
+// Host-side table of the filter kernel configurations and the launchers of
+// every kernel in the library.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "pf_internal.cuh"
+
+namespace pf {
+
+// One batched-filter configuration: TPP lanes per pair, DPT diagonal slots
+// per lane; it serves thresholds E <= ecap.
+struct KernelCfg {
+    int tpp, dpt, ecap;
+};
+
+constexpr KernelCfg kBatchCfgs[] = {
+    {1, 4, 3},   {2, 4, 3},   {4, 2, 3},   {8, 1, 3},
+    {1, 8, 7},   {2, 8, 7},   {4, 4, 7},   {8, 2, 7},  {16, 1, 7},
+    {1, 16, 15}, {2, 16, 15}, {4, 8, 15},  {8, 4, 15}, {16, 2, 15}, {32, 1, 15},
+    {2, 32, 31}, {4, 16, 31}, {8, 8, 31},  {16, 4, 31}, {32, 2, 31},
+};
+constexpr int kNumBatchCfgs = sizeof(kBatchCfgs) / sizeof(kBatchCfgs[0]);
+
+// Plain kernel (one thread per pair): DPT = kPlainDpt[i] serves E <= DPT - 1.
+constexpr int kPlainDpt[] = {1, 2, 4, 8, 16, 32};
+constexpr int kNumPlain = sizeof(kPlainDpt) / sizeof(kPlainDpt[0]);
+
+// dec in {1, 2, 3}
+cudaError_t launch_filter_plain(int dec, int plain_idx, const FilterArgs &a, cudaStream_t st);
+cudaError_t launch_filter_batched(int dec, int cfg, int grid, const BatchArgs &b, int bin,
+                                  cudaStream_t st);
+const void *filter_batched_fn(int dec, int cfg);
+
+cudaError_t launch_pack_ragged(const uint8_t *ascii, const int64_t *byte_off,
+                               const int64_t *word_off, int64_t nseq, uint32_t *lo,
+                               uint32_t *hi, uint32_t *nm, unsigned *err, cudaStream_t st);
+cudaError_t launch_pack_fixed(const uint8_t *ascii, int64_t nseq, int len, uint32_t *lo,
+                              uint32_t *hi, uint32_t *nm, unsigned *err, int sms,
+                              cudaStream_t st);
+int64_t compact_tiles(int64_t n);
+cudaError_t launch_compact(const uint8_t *flags, int64_t n, int64_t *idx, int64_t *n_out,
+                           int64_t *tile_scratch, cudaStream_t st);
+cudaError_t launch_verify(const PairsView &pv, const int32_t *lens, const int16_t *E, int E_max,
+                          const int64_t *idx, const int64_t *n_idx, int64_t n, int32_t *dist,
+                          unsigned *err, int sms, cudaStream_t st);
+
+}  // namespace pf

@@ -1,0 +1,59 @@
+"""The C-ABI library builds for sm_103a and exports every entry point that
+include/pf.h declares (no GPU needed: nothing is called)."""
+import ctypes
+import os
+import re
+
+from conftest import ROOT
+
+
+def declared_symbols():
+    with open(os.path.join(ROOT, "include", "pf.h")) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"PF_API\s+[^;(]*?\b(pf_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for required in ("pf_create", "pf_destroy", "pf_pack", "pf_filter", "pf_verify",
+                     "pf_compact", "pf_filter_plain", "pf_filter_verify", "pf_sync"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1910_03936_gb300 import build
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    missing = [n for n in declared_symbols() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings_without_gpu():
+    from paper_1910_03936_gb300 import build
+    lib = ctypes.CDLL(build.build())
+    lib.pf_status_string.restype = ctypes.c_char_p
+    assert lib.pf_status_string(0) == b"PF_OK"
+    assert lib.pf_status_string(7) == b"PF_EDATA"
+
+
+def test_pack_layout_host_helper():
+    import numpy as np
+    from paper_1910_03936_gb300 import build
+    lib = ctypes.CDLL(build.build())
+    bo = np.array([0, 0, 1, 32, 33, 97, 97], dtype=np.int64)
+    wo = np.zeros(7, dtype=np.int64)
+    tot = ctypes.c_int64()
+    rc = lib.pf_pack_layout(ctypes.c_void_p(bo.ctypes.data), ctypes.c_int64(6),
+                            ctypes.c_void_p(wo.ctypes.data), ctypes.byref(tot))
+    assert rc == 0
+    assert wo.tolist() == [0, 0, 1, 2, 3, 5, 5] and tot.value == 5
+
+
+def test_product_path_never_imports_oracle():
+    pkg = os.path.join(ROOT, "paper_1910_03936_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for fn in files:
+            if fn.endswith((".py", ".cu", ".cuh", ".h")):
+                with open(os.path.join(dirpath, fn)) as f:
+                    src = f.read()
+                assert "oracle" not in src.replace("oracle-free", ""), fn

@@ -1,0 +1,365 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Sizes span several tiles and warps with ragged tails; every kernel
+configuration of the batch scheduler is exercised; edge cases cover empty
+pairs, lengths around word boundaries, E = 0, E >= length, all-N and
+lower-case input, invalid bytes and invalid per-pair thresholds.  Accept
+flags, counts, packed words, indices and distances must be bit-exact.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from conftest import ArrayPairs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pf():
+    from paper_1910_03936_gb300 import build
+    build.build()
+    import paper_1910_03936_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(pf):
+    c = pf.pf_create(0)
+    yield c
+    pf.pf_destroy(c)
+
+
+def explicit_pairs(items):
+    """synth.Pairs from a list of (read, ref, E)."""
+    reads = b"".join(r.encode() for r, _, _ in items)
+    refs = b"".join(f.encode() for _, f, _ in items)
+    lens = np.array([len(r) for r, _, _ in items], dtype=np.int32)
+    off = np.zeros(len(items) + 1, dtype=np.int64)
+    np.cumsum(lens, out=off[1:])
+    E = np.array([e for _, _, e in items], dtype=np.int16)
+    return synth.Pairs(np.frombuffer(reads, np.uint8).copy() if reads else np.zeros(0, np.uint8),
+                       np.frombuffer(refs, np.uint8).copy() if refs else np.zeros(0, np.uint8),
+                       off, off, lens, E)
+
+
+def edge_items():
+    rng = np.random.default_rng(2024)
+    items = [("", "", 0), ("", "", 5), ("A", "A", 0), ("A", "C", 0), ("N", "N", 0),
+             ("N", "N", 1), ("ACG", "ACG", 9), ("ACG", "TTT", 20), ("acgtn", "ACGTN", 1),
+             ("GGTGAGAGTTGT", "GGTGGAGAGATC", 3), ("GGTGAGAGTTGT", "GGTGGAGAGATC", 2),
+             ("N" * 40, "N" * 40, 31), ("A" * 64, "A" * 64, 0), ("A" * 64, "A" * 63 + "C", 0)]
+    for L in (31, 32, 33, 63, 64, 65, 95, 96, 97, 127, 128, 129, 255, 256, 257, 300, 511, 1000):
+        for E in (0, 1, 3, 7, 15, 31):
+            ref = "".join(rng.choice(list("ACGT"), size=L))
+            read = list(ref)
+            for _ in range(int(rng.integers(0, E + 3))):
+                pos = int(rng.integers(0, max(len(read), 1)))
+                op = rng.random()
+                if not read:
+                    read.append("A")
+                elif op < 0.5:
+                    read[pos] = str(rng.choice(list("ACGTN")))
+                elif op < 0.75:
+                    read.insert(pos, str(rng.choice(list("ACGT"))))
+                else:
+                    del read[pos]
+            read = ("".join(read) + ref)[:L]
+            items.append((read, ref, E))
+    return items
+
+
+def oracle_filter(P, deciders):
+    return oracle.filter_batch(P, deciders=deciders)
+
+
+# ---- a1 pack ---------------------------------------------------------------
+
+def test_pack_ragged_matches_oracle(pf, ctx):
+    from gpu_util import to_dev
+    P = synth.generate(synth.MIXED, 11, 3000)
+    P2 = explicit_pairs(edge_items())
+    for src, off in ((P.reads, P.read_off), (P2.refs, P2.ref_off)):
+        wo, total = pf.pf_pack_layout(off)
+        out = pf.Seqs.empty(total, "cuda:0", word_off=to_dev(wo))
+        pf.pf_pack(ctx, to_dev(src if len(src) else np.zeros(1, np.uint8)), to_dev(off),
+                   to_dev(wo), out)
+        pf.pf_sync(ctx)
+        owo, lo, hi, nm, bad = oracle.pack_batch(src, off)
+        assert bad == 0
+        assert np.array_equal(owo, wo)
+        for got, want in ((out.lo, lo), (out.hi, hi), (out.nmask, nm)):
+            assert np.array_equal(got.cpu().numpy()[:total].view(np.uint32), want)
+
+
+@pytest.mark.parametrize("length", [1, 31, 32, 33, 100, 150, 250, 257])
+def test_pack_fixed_matches_oracle(pf, ctx, length):
+    from gpu_util import to_dev
+    rng = np.random.default_rng(length)
+    n = 777
+    src = rng.choice(np.frombuffer(b"ACGTNacgtn", np.uint8), size=n * length)
+    W = (length + 31) // 32
+    out = pf.Seqs.empty(n * W, "cuda:0", stride_words=W)
+    pf.pf_pack_fixed(ctx, to_dev(src), n, length, out)
+    pf.pf_sync(ctx)
+    off = np.arange(n + 1, dtype=np.int64) * length
+    _, lo, hi, nm, _ = oracle.pack_batch(src, off)
+    for got, want in ((out.lo, lo), (out.hi, hi), (out.nmask, nm)):
+        assert np.array_equal(got.cpu().numpy().view(np.uint32), want)
+
+
+def test_pack_unaligned_source(pf, ctx):
+    from gpu_util import to_dev
+    rng = np.random.default_rng(5)
+    base = to_dev(rng.choice(np.frombuffer(b"ACGT", np.uint8), size=5000))
+    for shift in (1, 2, 3, 5):
+        src = base[shift:shift + 150 * 20]
+        out = pf.Seqs.empty(20 * 5, "cuda:0", stride_words=5)
+        pf.pf_pack_fixed(ctx, src, 20, 150, out)
+        pf.pf_sync(ctx)
+        host = base.cpu().numpy()[shift:shift + 3000]
+        _, lo, hi, nm, _ = oracle.pack_batch(host, np.arange(21, dtype=np.int64) * 150)
+        assert np.array_equal(out.lo.cpu().numpy().view(np.uint32), lo)
+        assert np.array_equal(out.nmask.cpu().numpy().view(np.uint32), nm)
+
+
+def test_pack_invalid_bytes_report_and_pack_as_n(pf, ctx):
+    from gpu_util import to_dev
+    seq = np.frombuffer(b"ACGTXACGT-ACGU" + b"A" * 30, np.uint8).copy()
+    off = np.array([0, len(seq)], dtype=np.int64)
+    wo, total = pf.pf_pack_layout(off)
+    out = pf.Seqs.empty(total, "cuda:0", word_off=to_dev(wo))
+    pf.pf_pack(ctx, to_dev(seq), to_dev(off), to_dev(wo), out)
+    with pytest.raises(pf.PFError) as ei:
+        pf.pf_sync(ctx)
+    assert ei.value.status == 7
+    _, lo, hi, nm, bad = oracle.pack_batch(seq, off)
+    assert bad == 3
+    assert np.array_equal(out.nmask.cpu().numpy()[:total].view(np.uint32), nm)
+    assert np.array_equal(out.lo.cpu().numpy()[:total].view(np.uint32), lo)
+
+
+# ---- a2-a4 filter ---------------------------------------------------------
+
+CASES = [
+    ("cfg1_uniform_100bp_E5", synth.UNIFORM, 100, 5, 20, 20000),
+    ("cfg2_150bp_E0", synth.SKEWED, 150, 0, 60, 12000),
+    ("cfg2_150bp_E1", synth.SKEWED, 150, 1, 60, 12000),
+    ("cfg2_150bp_E6", synth.SKEWED, 150, 6, 60, 20000),
+    ("cfg2_150bp_E11", synth.SKEWED, 150, 11, 60, 12000),
+    ("cfg2_150bp_E15", synth.SKEWED, 150, 15, 60, 12000),
+    ("cfg3_mixed", synth.MIXED, 0, 0, 60, 30000),
+    ("cfg4_250bp_E25", synth.SKEWED_ALL, 250, 25, 100, 6000),
+]
+
+
+@pytest.fixture(scope="module")
+def case_data(ctx):
+    from gpu_util import DevicePairs
+    out = {}
+    for name, kind, m, E, kmax, n in CASES:
+        P = synth.generate(kind, 0x5EED0000 + 17 * E + m, n, m=m, E=E, kmax=kmax)
+        fixed = m if kind != synth.MIXED else None
+        D = DevicePairs(ctx, P, fixed=fixed)
+        out[name] = (P, D, oracle_filter(P, 3))
+    return out
+
+
+@pytest.mark.parametrize("name", [c[0] for c in CASES])
+@pytest.mark.parametrize("plain", [True, False])
+def test_filter_both_deciders_bit_exact(ctx, case_data, name, plain):
+    from gpu_util import filter_dev
+    P, D, (oa, oc) = case_data[name]
+    a, c = filter_dev(ctx, D, 3, plain=plain)
+    assert np.array_equal(c, oc), np.argwhere(c != oc)[:5]
+    assert np.array_equal(a, oa)
+
+
+@pytest.mark.parametrize("name", ["cfg2_150bp_E6", "cfg3_mixed", "cfg4_250bp_E25"])
+@pytest.mark.parametrize("dec", [1, 2])
+@pytest.mark.parametrize("plain", [True, False])
+def test_filter_single_decider(ctx, case_data, name, dec, plain):
+    from gpu_util import filter_dev
+    P, D, (oa, oc) = case_data[name]
+    a, c = filter_dev(ctx, D, dec, plain=plain)
+    slot = 0 if dec == 1 else 1
+    assert np.array_equal(c[0], oc[slot])
+    assert np.array_equal(a[0], oa[slot])
+
+
+def test_filter_uniform_E_without_array(ctx, case_data):
+    from gpu_util import filter_dev
+    P, D, (oa, oc) = case_data["cfg2_150bp_E6"]
+    for plain in (True, False):
+        a, c = filter_dev(ctx, D, 3, plain=plain, per_pair_E=False)
+        assert np.array_equal(c, oc) and np.array_equal(a, oa)
+
+
+def test_every_batched_configuration(pf, ctx):
+    """Each (lanes per pair, slots per lane) kernel, each decider set, at the
+    thresholds it serves, against the oracle."""
+    from gpu_util import DevicePairs, filter_dev
+    cfgs = pf.pf_kernel_configs()
+    data = {}
+    for E in (0, 2, 3, 5, 7, 12, 15, 20, 31):
+        P = synth.generate(synth.SKEWED, 900 + E, 2500, m=150 if E < 20 else 250, E=E,
+                           kmax=max(60, 3 * E))
+        data[E] = (P, DevicePairs(ctx, P, fixed=int(P.lens[0])), oracle_filter(P, 3))
+    for ci, (tpp, dpt, ecap) in enumerate(cfgs):
+        for E, (P, D, (oa, oc)) in data.items():
+            if E > ecap or E < ecap // 2 - 1:
+                continue
+            for dec in (1, 2, 3):
+                for chunk in (32, 1000):
+                    pf.pf_tune_set(ctx, dec, E, ci, chunk)
+                    a, c = filter_dev(ctx, D, dec, per_pair_E=False, E_max=E)
+                    want_c = oc if dec == 3 else oc[[0 if dec == 1 else 1]]
+                    want_a = oa if dec == 3 else oa[[0 if dec == 1 else 1]]
+                    assert np.array_equal(c, want_c), (ci, tpp, dpt, E, dec, chunk)
+                    assert np.array_equal(a, want_a), (ci, tpp, dpt, E, dec, chunk)
+
+
+def test_ragged_mixed_E_with_several_configs(pf, ctx, case_data):
+    """Per-pair E spread over three kernel configurations in one call."""
+    from gpu_util import filter_dev
+    P, D, (oa, oc) = case_data["cfg3_mixed"]
+    cfgs = pf.pf_kernel_configs()
+    pick = {e: next(i for i, c in enumerate(cfgs) if c[2] >= e and c[0] == (4 if e > 7 else 1))
+            for e in range(0, 21)}
+    for e, ci in pick.items():
+        pf.pf_tune_set(ctx, 3, e, ci, 128)
+    a, c = filter_dev(ctx, D, 3)
+    assert np.array_equal(c, oc) and np.array_equal(a, oa)
+
+
+def test_edge_cases(ctx):
+    from gpu_util import DevicePairs, filter_dev
+    P = explicit_pairs(edge_items())
+    D = DevicePairs(ctx, P)
+    oa, oc = oracle_filter(P, 3)
+    for plain in (True, False):
+        a, c = filter_dev(ctx, D, 3, plain=plain)
+        assert np.array_equal(c, oc), np.argwhere(c != oc)[:5]
+        assert np.array_equal(a, oa)
+    # worked example of Fig. 8.1/8.2: three obstacles at E = 3
+    i = [k for k, it in enumerate(edge_items()) if it[0] == "GGTGAGAGTTGT" and it[2] == 3][0]
+    assert c[0][i] == 3 and a[0][i] == 1
+
+
+def test_invalid_per_pair_threshold(pf, ctx):
+    from gpu_util import DevicePairs, filter_dev
+    P = explicit_pairs([("ACGT", "ACGT", 2), ("ACGT", "ACGA", 9), ("ACGT", "ACGT", 1)])
+    D = DevicePairs(ctx, P)
+    D.E_max = 3  # the second pair's E = 9 exceeds it
+    for plain in (True, False):
+        with pytest.raises(pf.PFError) as ei:
+            filter_dev(ctx, D, 3, plain=plain)
+        assert ei.value.status == 1
+        pf.pf_sync(ctx)
+
+
+def test_host_checks_reject_bad_arguments(pf, ctx, case_data):
+    P, D, _ = case_data["cfg2_150bp_E6"]
+    acc = torch.zeros(2 * D.n, dtype=torch.uint8, device="cuda:0")
+    cnt = torch.zeros(2 * D.n, dtype=torch.int16, device="cuda:0")
+    with pytest.raises(pf.PFError):
+        pf.pf_filter(ctx, 3, D.pairs, D.lens, D.E, 32, acc, cnt, D.n)
+    with pytest.raises(pf.PFError):
+        pf.pf_filter(ctx, 4, D.pairs, D.lens, D.E, 6, acc, cnt, D.n)
+    with pytest.raises(pf.PFError):
+        pf.pf_tune_set(ctx, 1, 20, 0, 64)  # configuration 0 serves E <= 3
+
+
+# ---- a5 compaction ----------------------------------------------------------
+
+@pytest.mark.parametrize("n", [0, 1, 15, 16, 17, 4095, 4096, 4097, 100003])
+@pytest.mark.parametrize("offset", [0, 3])
+def test_compact_matches_nonzero(pf, ctx, n, offset):
+    rng = np.random.default_rng(n + offset)
+    flags = (rng.random(n + offset) < 0.3).astype(np.uint8)
+    flags[offset:] *= rng.integers(1, 255, size=n).astype(np.uint8)
+    f = torch.from_numpy(flags).cuda()[offset:]
+    idx = torch.full((max(n, 1),), -1, dtype=torch.int64, device="cuda:0")
+    n_out = torch.full((1,), -1, dtype=torch.int64, device="cuda:0")
+    pf.pf_compact(ctx, f, idx, n_out, n)
+    pf.pf_sync(ctx)
+    want = np.nonzero(flags[offset:])[0]
+    k = int(n_out.item())
+    assert k == len(want)
+    assert np.array_equal(idx.cpu().numpy()[:k], want)
+
+
+# ---- a6 verification -----------------------------------------------------------
+
+@pytest.mark.parametrize("name", [c[0] for c in CASES])
+def test_verify_all_pairs_bit_exact(ctx, case_data, name):
+    from gpu_util import verify_dev
+    P, D, _ = case_data[name]
+    d = verify_dev(ctx, D)
+    assert np.array_equal(d, oracle.verify_batch(P)), name
+
+
+def test_verify_edge_cases_and_subset(ctx):
+    from gpu_util import DevicePairs, verify_dev
+    P = explicit_pairs(edge_items())
+    D = DevicePairs(ctx, P)
+    want = oracle.verify_batch(P)
+    assert np.array_equal(verify_dev(ctx, D), want)
+    sub = np.arange(0, P.n, 3)
+    got = verify_dev(ctx, D, idx=sub)
+    assert np.array_equal(got[sub], want[sub])
+    rest = np.setdiff1d(np.arange(P.n), sub)
+    assert np.all(got[rest] == -9)   # untouched
+    # equals the unbanded distance wherever that is <= E
+    wf = oracle.int_batch("wf", P)
+    assert np.array_equal(np.minimum(wf, P.E.astype(np.int32) + 1), want)
+
+
+def test_verify_exhaustive_tiny(ctx):
+    """All pairs over {A,C,G,N}^4 at E = 0..4 (Levenshtein vs the banded
+    bit-vector kernel)."""
+    from conftest import all_pairs
+    from gpu_util import DevicePairs, verify_dev
+    reads, refs = all_pairs("ACGN", 4)
+    for E in range(0, 5):
+        P = ArrayPairs(reads, refs, E)
+        sp = synth.Pairs(P.reads, P.refs, P.read_off, P.ref_off, P.lens, P.E)
+        D = DevicePairs(ctx, sp, fixed=4)
+        assert np.array_equal(verify_dev(ctx, D), oracle.verify_batch(sp))
+
+
+# ---- a2-a6 whole path --------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["cfg2_150bp_E6", "cfg3_mixed", "cfg4_250bp_E25"])
+def test_filter_verify_path(pf, ctx, case_data, name):
+    P, D, (oa, oc) = case_data[name]
+    n = D.n
+    acc = torch.zeros(2 * n, dtype=torch.uint8, device="cuda:0")
+    cnt = torch.zeros(2 * n, dtype=torch.int16, device="cuda:0")
+    dist = torch.full((n,), -5, dtype=torch.int32, device="cuda:0")
+    pf.pf_filter_verify(ctx, 3, D.pairs, D.lens, D.E, D.E_max, acc, cnt, dist, n)
+    pf.pf_sync(ctx)
+    a = acc.cpu().numpy().reshape(2, n)
+    assert np.array_equal(a, oa)
+    d = dist.cpu().numpy()
+    vb = oracle.verify_batch(P)
+    E1 = P.E.astype(np.int32) + 1
+    want = np.where(oa[0] == 1, vb, E1)
+    assert np.array_equal(d, want)
+    # zero false rejects: every pair within E survives with its exact distance
+    assert np.all(oa[0][vb <= P.E] == 1)
+
+
+# ---- scheduler tuning ------------------------------------------------------------
+
+def test_tuner_picks_a_valid_config_and_stays_exact(pf, ctx, case_data):
+    from gpu_util import filter_dev
+    P, D, (oa, oc) = case_data["cfg2_150bp_E6"]
+    cfg, chunk, ms = pf.pf_tune(ctx, 3, D.pairs, D.lens, 6, reps=1)
+    tpp, dpt, ecap = pf.pf_kernel_configs()[cfg]
+    assert ecap >= 6 and ms > 0 and chunk in (64, 256, 1024)
+    assert pf.pf_tune_get(ctx, 3, 6) == (cfg, chunk)
+    a, c = filter_dev(ctx, D, 3)
+    assert np.array_equal(c, oc) and np.array_equal(a, oa)
