@@ -19,7 +19,7 @@ __all__ = [
     "pf_create", "pf_destroy", "pf_set_stream", "pf_sync", "pf_last_error",
     "pf_pack_layout", "pf_pack", "pf_pack_fixed", "pf_filter", "pf_filter_plain",
     "pf_compact", "pf_verify", "pf_filter_verify", "library_path", "load", "pack_pairs",
-    "pf_kernel_configs", "pf_tune_set", "pf_tune_get", "pf_tune",
+    "pf_kernel_configs", "pf_tune_set", "pf_tune_get", "pf_tune", "pf_compact_noalloc",
 ]
 
 PF_SNEAKYSNAKE = 1
@@ -79,6 +79,7 @@ def load():
         "pf_filter": [P, U, ctypes.POINTER(_Pairs), P, P, I, P, P, I64],
         "pf_filter_plain": [P, U, ctypes.POINTER(_Pairs), P, P, I, P, P, I64],
         "pf_compact": [P, P, I64, P, P],
+        "pf_compact_noalloc": [P, I64, P, P, P],
         "pf_verify": [P, ctypes.POINTER(_Pairs), P, P, I, P, P, I64, P],
         "pf_filter_verify": [P, U, ctypes.POINTER(_Pairs), P, P, I, P, P, P, I64],
         "pf_kernel_configs": [P, P, P, I, ctypes.POINTER(ctypes.c_int)],
@@ -259,6 +260,19 @@ def pf_compact(ctx, flags, idx, n_out, n=None):
     n = flags.numel() if n is None else n
     _cur_stream(ctx)
     _check(load().pf_compact(ctx.handle, _p(flags), int(n), _p(idx), _p(n_out)), ctx.handle)
+
+
+def pf_compact_noalloc(flags, idx, n_out, n=None, stream=None):
+    """pf_compact without a context and without any device allocation
+    (fixed in-library counters, n <= 134,217,728; concurrent calls race)."""
+    _dt(flags, torch.uint8, "flags")
+    _dt(idx, torch.int64, "idx")
+    _dt(n_out, torch.int64, "n_out")
+    n = flags.numel() if n is None else n
+    if stream is None:
+        stream = torch.cuda.current_stream(flags.device).cuda_stream
+    _check(load().pf_compact_noalloc(_p(flags), int(n), _p(idx), _p(n_out),
+                                     ctypes.c_void_p(int(stream))))
 
 
 def pf_verify(ctx, pairs, lens, E, E_max, idx, n_idx, dist, n=None):
