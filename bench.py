@@ -68,7 +68,7 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -202,10 +202,19 @@ def main_gpu(args):
     # tune the batched kernel for this threshold on a sample of the batch
     pf.pf_pack_fixed(ctx, reads, n, M, rd)
     pf.pf_pack_fixed(ctx, refs, n, M, rf)
-    tune_n = min(n, 2_000_000)
     tuned = {}
-    for dec in (1, 3):
-        tuned[dec] = pf.pf_tune(ctx, dec, pairs, lens, E_HEAD, n=tune_n, reps=2)
+    if args.cfg is not None:
+        for dec in (1, 2, 3):
+            pf.pf_tune_set(ctx, dec, E_HEAD, args.cfg, args.chunk)
+            tuned[dec] = (args.cfg, args.chunk, None)
+    elif not args.no_tune:
+        tune_n = min(n, 2_000_000)
+        for dec in (1, 3):
+            tuned[dec] = pf.pf_tune(ctx, dec, pairs, lens, E_HEAD, n=tune_n, reps=2)
+    else:
+        for dec in (1, 2, 3):
+            c, k = pf.pf_tune_get(ctx, dec, E_HEAD)
+            tuned[dec] = (c, k, None)
 
     ev = lambda: torch.cuda.Event(enable_timing=True)
     stage_names = ("pack", "filter", "compact_verify")
@@ -248,6 +257,33 @@ def main_gpu(args):
         ms = float(tt.item())
     pack_ms = statistics.mean(r[0].elapsed_time(r[1]) for r in recs)
     fv_ms = statistics.mean(r[1].elapsed_time(r[3]) for r in recs)
+    if args.stage != "step":
+        dec = args.deciders
+        fn = pf.pf_filter_plain if args.stage == "filter_plain" else pf.pf_filter
+        # one threshold for every pair: no per-pair E array, one kernel launch
+        for _ in range(args.warmup):
+            fn(ctx, dec, pairs, lens, None, E_HEAD, acc, cnt, n)
+        a0, a1 = ev(), ev()
+        a0.record(stream)
+        for _ in range(args.steps):
+            fn(ctx, dec, pairs, lens, None, E_HEAD, acc, cnt, n)
+        a1.record(stream)
+        torch.cuda.synchronize(dev)
+        fms = a0.elapsed_time(a1) / args.steps
+        if rank == 0:
+            print(json.dumps({"stage": args.stage, "deciders": dec, "ms": fms,
+                              "pairs_s": n / (fms / 1000.0), "cfg": list(tuned[dec if dec in tuned else 1])}),
+                  flush=True)
+        pf.pf_destroy(ctx)
+        return
+    if args.no_extras:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": n * world / (ms / 1000.0),
+                              "unit": "pairs/s", "ms_per_step": ms, "pack_ms": pack_ms,
+                              "filter_verify_ms": fv_ms, "clocks": clk,
+                              "mode": "step only (profiling)"}), flush=True)
+        pf.pf_destroy(ctx)
+        return
 
     # per-kernel split of filter vs compact+verify: time them separately
     def timed(fn, reps=args.steps):
@@ -358,12 +394,20 @@ def main_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--pairs", type=int, default=N_PAIRS)
     ap.add_argument("--cpu-sample", type=int, default=400_000)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default kernel choice")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="time the step only (for profiling): no side measurements")
+    ap.add_argument("--cfg", type=int, default=None, help="force batch kernel configuration")
+    ap.add_argument("--chunk", type=int, default=64)
+    ap.add_argument("--stage", default="step", choices=["step", "filter_plain", "filter_batched"],
+                    help="time one filter kernel instead of the step (profiling)")
+    ap.add_argument("--deciders", type=int, default=3)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

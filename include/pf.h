@@ -179,10 +179,11 @@ PF_API pf_status pf_filter_plain(pf_ctx *ctx, unsigned deciders, const pf_pairs 
 /* ---- a7: scheduler tuning --------------------------------------------------- */
 
 /* Kernel configurations of the batch scheduler.  Writes up to cap entries
- * (lanes per pair, diagonal slots per lane, largest E served) into the
- * host arrays (any may be NULL) and the number of configurations into
- * *count. */
-PF_API pf_status pf_kernel_configs(int *tpp, int *dpt, int *ecap, int cap, int *count);
+ * (lanes per pair, diagonal slots per lane, largest E served, and the one
+ * E an exact-threshold configuration serves or -1) into the host arrays
+ * (any may be NULL) and the number of configurations into *count. */
+PF_API pf_status pf_kernel_configs(int *tpp, int *dpt, int *ecap, int *exact_e, int cap,
+                                   int *count);
 
 /* Use configuration cfg and a work chunk of `chunk` pairs (1..65536) for
  * threshold E under decider set `deciders` in later pf_filter calls.

@@ -82,7 +82,7 @@ def load():
         "pf_compact_noalloc": [P, I64, P, P, P],
         "pf_verify": [P, ctypes.POINTER(_Pairs), P, P, I, P, P, I64, P],
         "pf_filter_verify": [P, U, ctypes.POINTER(_Pairs), P, P, I, P, P, P, I64],
-        "pf_kernel_configs": [P, P, P, I, ctypes.POINTER(ctypes.c_int)],
+        "pf_kernel_configs": [P, P, P, P, I, ctypes.POINTER(ctypes.c_int)],
         "pf_tune_set": [P, U, I, I, I],
         "pf_tune_get": [P, U, I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
         "pf_tune": [P, U, ctypes.POINTER(_Pairs), P, I, I64, I, ctypes.POINTER(ctypes.c_int),
@@ -334,14 +334,15 @@ def pack_pairs(ctx, reads, refs, length=None, byte_off=None):
 
 
 def pf_kernel_configs():
-    """List of (tpp, dpt, ecap) of the batch scheduler's kernels."""
+    """List of (tpp, dpt, ecap, exact_e) of the batch scheduler's kernels;
+    exact_e >= 0 marks a kernel that serves that threshold only."""
     import numpy as np
     cnt = ctypes.c_int()
-    _check(load().pf_kernel_configs(None, None, None, 0, ctypes.byref(cnt)))
-    a = [np.zeros(cnt.value, dtype=np.int32) for _ in range(3)]
+    _check(load().pf_kernel_configs(None, None, None, None, 0, ctypes.byref(cnt)))
+    a = [np.zeros(cnt.value, dtype=np.int32) for _ in range(4)]
     _check(load().pf_kernel_configs(*[ctypes.c_void_p(x.ctypes.data) for x in a], cnt.value,
                                     ctypes.byref(cnt)))
-    return [(int(a[0][i]), int(a[1][i]), int(a[2][i])) for i in range(cnt.value)]
+    return [tuple(int(x[i]) for x in a) for i in range(cnt.value)]
 
 
 def pf_tune_set(ctx, deciders, E, cfg, chunk):

@@ -24,11 +24,12 @@ struct BinTable {
 
 __global__ void bin_init_kernel(int64_t *bin_start, unsigned long long *work,
                                 unsigned long long *hist, int nb, int single_cfg, int64_t n) {
-    const int i = threadIdx.x;
-    if (i <= nb) bin_start[i] = (single_cfg >= 0) ? (i <= single_cfg ? 0 : n) : 0;
-    if (i < nb) {
-        work[i] = 0ull;
-        hist[i] = 0ull;
+    for (int i = threadIdx.x; i <= nb; i += blockDim.x) {
+        bin_start[i] = (single_cfg >= 0) ? (i <= single_cfg ? 0 : n) : 0;
+        if (i < nb) {
+            work[i] = 0ull;
+            hist[i] = 0ull;
+        }
     }
 }
 
@@ -51,16 +52,22 @@ bin_hist_kernel(const int16_t *E, int64_t n, int E_max, BinTable t, unsigned lon
         if (cnt[i]) atomicAdd(&hist[i], (unsigned long long)cnt[i]);
 }
 
+// Exclusive scan of the bin sizes.  When every pair falls in one bin the
+// grouping is the identity: `ident` tells the scatter to skip and the
+// filter to index pairs directly.
 __global__ void bin_scan_kernel(const unsigned long long *hist, int64_t *bin_start,
-                                unsigned long long *cursor) {
+                                unsigned long long *cursor, int *ident) {
     if (threadIdx.x != 0) return;
     int64_t acc = 0;
+    int used = 0;
     for (int i = 0; i < kNumBatchCfgs; ++i) {
         bin_start[i] = acc;
         cursor[i] = (unsigned long long)acc;
         acc += (int64_t)hist[i];
+        used += hist[i] ? 1 : 0;
     }
     bin_start[kNumBatchCfgs] = acc;
+    *ident = (used <= 1);
 }
 
 // Each block claims room for its pairs per bin with one atomic per bin and
@@ -68,9 +75,10 @@ __global__ void bin_scan_kernel(const unsigned long long *hist, int64_t *bin_sta
 // pair keeps its own index, so results do not depend on it).
 __global__ void __launch_bounds__(256)
 bin_scatter_kernel(const int16_t *E, int64_t n, int E_max, BinTable t,
-                   unsigned long long *cursor, int64_t *order) {
+                   unsigned long long *cursor, int64_t *order, const int *ident) {
     __shared__ unsigned cnt[kNumBatchCfgs];
     __shared__ unsigned long long base[kNumBatchCfgs];
+    if (*ident) return;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (int i = threadIdx.x; i < kNumBatchCfgs; i += blockDim.x) cnt[i] = 0;
     __syncthreads();
@@ -163,6 +171,7 @@ pf_status pf_ctx::scratch_layout(int64_t n, Scratch *s) {
     const size_t o_work = off;  off += up(kNumBatchCfgs * sizeof(unsigned long long));
     const size_t o_hist = off;  off += up(kNumBatchCfgs * sizeof(unsigned long long));
     const size_t o_cur = off;   off += up(kNumBatchCfgs * sizeof(unsigned long long));
+    const size_t o_ident = off; off += up(sizeof(int));
     pf_status st = ensure_scratch(off);
     if (st != PF_OK) return st;
     char *b = static_cast<char *>(scratch);
@@ -174,6 +183,7 @@ pf_status pf_ctx::scratch_layout(int64_t n, Scratch *s) {
     s->work = reinterpret_cast<unsigned long long *>(b + o_work);
     s->hist = reinterpret_cast<unsigned long long *>(b + o_hist);
     s->cursor = reinterpret_cast<unsigned long long *>(b + o_cur);
+    s->ident = reinterpret_cast<int *>(b + o_ident);
     return PF_OK;
 }
 
@@ -187,18 +197,14 @@ int pf_ctx::grid_for(int dec, int cfg) {
     return g;
 }
 
-// Default configuration for threshold E before any tuning: the smallest
-// capacity that fits, one lane per pair up to E = 7, then wider groups.
+// Default configuration for threshold E before any tuning: the
+// exact-threshold one-thread kernel up to E = 15, eight lanes per pair
+// above.
 int pf::pf_default_cfg(int E) {
-    int want_tpp = E <= 7 ? 1 : (E <= 15 ? 4 : 8);
-    int best = -1;
-    for (int c = 0; c < kNumBatchCfgs; ++c) {
-        if (kBatchCfgs[c].ecap < E) continue;
-        if (best < 0 || kBatchCfgs[c].ecap < kBatchCfgs[best].ecap ||
-            (kBatchCfgs[c].ecap == kBatchCfgs[best].ecap && kBatchCfgs[c].tpp == want_tpp))
-            best = c;
-    }
-    return best;
+    if (E <= 15) return kFirstExactCfg + E;
+    for (int c = 0; c < kNumBatchCfgs; ++c)
+        if (kBatchCfgs[c].tpp == 8 && kBatchCfgs[c].xe < 0 && kBatchCfgs[c].ecap >= E) return c;
+    return -1;
 }
 
 void pf_ctx::reset_tuning() {
@@ -281,6 +287,7 @@ pf_status pf_ctx::run_batched(unsigned dec, const FilterArgs &a, const Scratch &
             b.order = nullptr;
         }
     }
+    b.ident = (single < 0) ? s.ident : nullptr;
     bin_init_kernel<<<1, 32, 0, stream>>>(s.bin_start, s.work, s.hist, kNumBatchCfgs, single,
                                           a.n);
     if (single < 0) {
@@ -289,9 +296,9 @@ pf_status pf_ctx::run_batched(unsigned dec, const FilterArgs &a, const Scratch &
         int64_t hb = std::min<int64_t>((a.n + 255) / 256, (int64_t)sms * 8);
         bin_hist_kernel<<<(unsigned)std::max<int64_t>(hb, 1), 256, 0, stream>>>(a.E, a.n, a.E_max,
                                                                                t, s.hist);
-        bin_scan_kernel<<<1, 32, 0, stream>>>(s.hist, s.bin_start, s.cursor);
+        bin_scan_kernel<<<1, 32, 0, stream>>>(s.hist, s.bin_start, s.cursor, s.ident);
         bin_scatter_kernel<<<(unsigned)((a.n + 255) / 256), 256, 0, stream>>>(
-            a.E, a.n, a.E_max, t, s.cursor, s.order);
+            a.E, a.n, a.E_max, t, s.cursor, s.order, s.ident);
     }
     pf_status st = cuda(cudaGetLastError(), "binning launch");
     if (st != PF_OK) return st;
@@ -552,12 +559,13 @@ pf_status pf_filter_verify(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs
                      "verify launch");
 }
 
-pf_status pf_kernel_configs(int *tpp, int *dpt, int *ecap, int cap, int *count) {
+pf_status pf_kernel_configs(int *tpp, int *dpt, int *ecap, int *exact_e, int cap, int *count) {
     if (!count || cap < 0) return PF_EINVAL;
     for (int c = 0; c < kNumBatchCfgs && c < cap; ++c) {
         if (tpp) tpp[c] = kBatchCfgs[c].tpp;
         if (dpt) dpt[c] = kBatchCfgs[c].dpt;
         if (ecap) ecap[c] = kBatchCfgs[c].ecap;
+        if (exact_e) exact_e[c] = kBatchCfgs[c].xe;
     }
     *count = kNumBatchCfgs;
     return PF_OK;
@@ -566,7 +574,7 @@ pf_status pf_kernel_configs(int *tpp, int *dpt, int *ecap, int cap, int *count) 
 pf_status pf_tune_set(pf_ctx *ctx, unsigned deciders, int E, int cfg, int chunk) {
     if (!ctx) return PF_EINVAL;
     if ((deciders & 3u) == 0 || (deciders & ~3u) || E < 0 || E > PF_MAX_E || cfg < 0 ||
-        cfg >= kNumBatchCfgs || kBatchCfgs[cfg].ecap < E || chunk < 1 || chunk > 65536)
+        cfg >= kNumBatchCfgs || !cfg_serves(kBatchCfgs[cfg], E) || chunk < 1 || chunk > 65536)
         return ctx->fail(PF_EINVAL, "pf_tune_set: bad deciders/E/cfg/chunk");
     ctx->tune_cfg[deciders][E] = cfg;
     ctx->tune_chunk[deciders][E] = chunk;
@@ -610,7 +618,7 @@ pf_status pf_tune(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs, const i
     float bms = 1e30f;
     static const int chunks[] = {64, 256, 1024};
     for (int c = 0; st == PF_OK && c < kNumBatchCfgs; ++c) {
-        if (kBatchCfgs[c].ecap < E) continue;
+        if (!cfg_serves(kBatchCfgs[c], E)) continue;
         for (int k : chunks) {
             ctx->tune_cfg[deciders][E] = c;
             ctx->tune_chunk[deciders][E] = k;

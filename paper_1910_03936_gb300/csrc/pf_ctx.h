@@ -16,6 +16,7 @@ namespace pf {
 struct Scratch {
     int64_t *order, *idx, *n_idx, *tiles, *bin_start;
     unsigned long long *work, *hist, *cursor;
+    int *ident;
 };
 
 struct ServeState;

@@ -1,5 +1,6 @@
 // Fused neighbourhood map + SneakySnake + GateKeeper for one pair, run by a
-// group of TPP lanes.  Included by the kernel instantiation units.
+// group of TPP lanes one 32-column word at a time.  Included by the kernel
+// instantiation units.
 //
 // Map (Eq. 6.1, Ch. 6 Discussion): for reference word w (columns 32w ..
 // 32w+31) and diagonal d, the mismatch word is
@@ -30,20 +31,27 @@
 // own d = -(1 + (g - TPP/2) + k*TPP/2), so every lane shifts its read
 // words from one fixed pair of words (sign fixed per lane).
 #pragma once
+#include <type_traits>
+
 #include "pf_internal.cuh"
 
 namespace pf {
 
-template <int TPP, int DPT>
+// XE >= 0 selects the exact-threshold form: one thread, E = XE fixed at
+// compile time, slots k = 0..XE hold d = k and slots XE+1..2XE hold
+// d = -(k - XE); every slot is live and every shift is a constant.
+template <int TPP, int DPT, int XE = -1>
 struct SlotMap {
-    static constexpr int NS = (TPP == 1) ? 2 * DPT : DPT;
+    static constexpr int NS = (XE >= 0) ? 2 * XE + 1 : ((TPP == 1) ? 2 * DPT : DPT);
     static constexpr int HALF = (TPP == 1) ? 1 : TPP / 2;
-    static constexpr int ECAP = DPT * HALF - 1;
+    static constexpr int ECAP = (XE >= 0) ? XE : DPT * HALF - 1;
 };
 
-template <int TPP, int DPT>
+template <int TPP, int DPT, int XE = -1>
 __device__ __forceinline__ int slot_d(int k, int g) {
-    if constexpr (TPP == 1) {
+    if constexpr (XE >= 0) {
+        return k <= XE ? k : -(k - XE);
+    } else if constexpr (TPP == 1) {
         return k < DPT ? k : -(1 + k - DPT);
     } else {
         constexpr int HALF = TPP / 2;
@@ -51,75 +59,104 @@ __device__ __forceinline__ int slot_d(int k, int g) {
     }
 }
 
+template <int TPP, int DPT, int XE>
+__device__ __forceinline__ bool slot_negative(int k, int g) {
+    if constexpr (XE >= 0) return k > XE;
+    else if constexpr (TPP == 1) return k >= DPT;
+    else return g >= TPP / 2;
+}
+
 __device__ __forceinline__ uint32_t shr_pair(uint32_t a, uint32_t b, int d) {
     // bits [r, r+32) of the 64-bit value b:a, r = d mod 32
     return __funnelshift_r(a, b, (unsigned)d & 31u);
 }
 
-struct Outputs {
-    int ss_count, gk_count;
-};
+__device__ __forceinline__ int imin(int a, int b) { return a < b ? a : b; }
 
-// DEC: bit 0 SneakySnake, bit 1 GateKeeper.
-template <int TPP, int DPT, int DEC>
-__device__ __forceinline__ Outputs filter_pair(const PairsView &pv, int64_t p, int m, int E,
-                                               int g, unsigned gmask) {
-    using SM = SlotMap<TPP, DPT>;
-    constexpr int NS = SM::NS;
-    constexpr bool SS = DEC & 1;
-    constexpr bool GK = DEC & 2;
+// The resumable state of one pair.  init() loads the first words, word()
+// processes one reference word and reports whether both deciders are
+// decided, finish() closes GateKeeper's last word.  Every lane of the
+// group holds the same copy of the scalar state.
+template <int TPP, int DPT, int DEC, int XE = -1>
+struct PairFilter {
+    using SM = SlotMap<TPP, DPT, XE>;
+    static constexpr int NS = SM::NS;
+    static constexpr bool SS = DEC & 1;
+    static constexpr bool GK = DEC & 2;
 
-    const int W = (m + 31) >> 5;
-    const int64_t rb = pv.read.start(p);
-    const int64_t fb = pv.ref.start(p);
+    int64_t rb, fb;
+    int m, E, W, w;
+    Word3 Rm1, R0, Rp1, Fw;
+    // one bit per slot
+    using Mask = typename std::conditional<(NS > 32), unsigned long long, uint32_t>::type;
 
-    int dd[NS];
-    bool live[NS];
-#pragma unroll
-    for (int k = 0; k < NS; ++k) {
-        dd[k] = slot_d<TPP, DPT>(k, g);
-        live[k] = (dd[k] <= E) && (-dd[k] <= E);
+    uint32_t Mp[NS], Mpp[NS];  // GateKeeper: mask words of words w-1 and w-2
+    Mask dead;            // SneakySnake: slots blocked before the current word
+    uint32_t C;           // SneakySnake: columns >= checkpoint in this word
+    int kss;
+    bool ss_done, gk_done, cont;
+    int h, fc;
+
+    __device__ __forceinline__ bool live(int k, int g) const {
+        if constexpr (XE >= 0) return true;
+        const int d = slot_d<TPP, DPT, XE>(k, g);
+        return d <= E && -d <= E;
     }
-    // lanes of a multi-lane group own diagonals of one sign
-    const bool lane_neg = (TPP > 1) && (g >= SM::HALF);
 
-    uint32_t M[NS], D[NS], Mp[NS], Mpp[NS];
+    // the threshold, a constant in the exact-threshold form
+    __device__ __forceinline__ int thr() const {
+        if constexpr (XE >= 0) return XE;
+        return E;
+    }
+
+    __device__ __forceinline__ void init(const PairsView &pv, int64_t p, int m_, int E_) {
+        m = m_;
+        E = E_;
+        W = (m + 31) >> 5;
+        w = 0;
+        rb = pv.read.start(p);
+        fb = pv.ref.start(p);
+        Rm1 = load_word(pv.read, rb, -1, W);
+        R0 = load_word(pv.read, rb, 0, W);
+        Rp1 = load_word(pv.read, rb, 1, W);
+        Fw = load_word(pv.ref, fb, 0, W);
 #pragma unroll
-    for (int k = 0; k < NS; ++k) { D[k] = 0u; Mp[k] = 0u; Mpp[k] = 0u; }
+        for (int k = 0; k < NS; ++k) { Mp[k] = 0u; Mpp[k] = 0u; }
+        dead = 0u;
+        C = 0xffffffffu;
+        kss = 0;
+        cont = false;
+        ss_done = !SS;
+        gk_done = !GK;
+        h = 0;
+        fc = 0;
+    }
 
-    // SneakySnake state (replicated on the group's lanes)
-    bool ss_done = !SS;
-    int kss = 0, ss_count = 0;
-    bool cont = false;
-    uint32_t C = 0xffffffffu;
-    // GateKeeper state
-    bool gk_done = !GK;
-    int h = 0, fc = 0, gk_count = 0;
+    __device__ __forceinline__ bool done() const { return (ss_done && gk_done) || w >= W; }
 
-    Word3 Rm1 = load_word(pv.read, rb, -1, W);
-    Word3 R0 = load_word(pv.read, rb, 0, W);
-    Word3 Rp1 = load_word(pv.read, rb, 1, W);
-
-    for (int w = 0; w < W; ++w) {
-        if (ss_done && gk_done) break;
-        const Word3 F = load_word(pv.ref, fb, w, W);
+    // Process reference word w; returns done().
+    __device__ __forceinline__ bool word(const PairsView &pv, int g, unsigned gmask) {
+        const Word3 F = Fw;
+        Fw = load_word(pv.ref, fb, w + 1, W);  // prefetch the next reference word
+        uint32_t M[NS];
         const uint32_t valid =
             (w == W - 1 && (m & 31)) ? ((1u << (m & 31)) - 1u) : 0xffffffffu;
 
         // ---- map words of this lane's diagonals
         Word3 A, B;
         if constexpr (TPP > 1) {
-            A.lo = lane_neg ? Rm1.lo : R0.lo;  B.lo = lane_neg ? R0.lo : Rp1.lo;
-            A.hi = lane_neg ? Rm1.hi : R0.hi;  B.hi = lane_neg ? R0.hi : Rp1.hi;
-            A.nm = lane_neg ? Rm1.nm : R0.nm;  B.nm = lane_neg ? R0.nm : Rp1.nm;
+            const bool neg = g >= SM::HALF;
+            A.lo = neg ? Rm1.lo : R0.lo;  B.lo = neg ? R0.lo : Rp1.lo;
+            A.hi = neg ? Rm1.hi : R0.hi;  B.hi = neg ? R0.hi : Rp1.hi;
+            A.nm = neg ? Rm1.nm : R0.nm;  B.nm = neg ? R0.nm : Rp1.nm;
         }
 #pragma unroll
         for (int k = 0; k < NS; ++k) {
-            if (!live[k]) continue;
-            const int d = dd[k];
+            if (!live(k, g)) continue;
+            const int d = slot_d<TPP, DPT, XE>(k, g);
             uint32_t slo, shi, snm;
             if constexpr (TPP == 1) {
-                if (k >= DPT) {  // negative diagonal: read words w-1, w
+                if (slot_negative<TPP, DPT, XE>(k, g)) {  // read words w-1, w
                     slo = shr_pair(Rm1.lo, R0.lo, d);
                     shi = shr_pair(Rm1.hi, R0.hi, d);
                     snm = shr_pair(Rm1.nm, R0.nm, d);
@@ -140,32 +177,30 @@ __device__ __forceinline__ Outputs filter_pair(const PairsView &pv, int64_t p, i
         if constexpr (SS) {
             if (!ss_done) {
                 bool word_done = false;
-                if (cont) {
+                if (cont) {  // a pipe runs on from an earlier word
                     uint32_t T = 0xffffffffu;
 #pragma unroll
                     for (int k = 0; k < NS; ++k) {
-                        if (!live[k]) continue;
-                        const uint32_t y = M[k] | D[k];
+                        if (!live(k, g)) continue;
+                        const uint32_t y = M[k] | (uint32_t)((dead >> k) & 1u);
                         T &= (y | (0u - y));
                     }
                     T = group_and<TPP>(T, gmask);
                     if (T == 0u) {
                         if (w == W - 1) {
                             ss_done = true;
-                            ss_count = kss;
                         } else {
 #pragma unroll
                             for (int k = 0; k < NS; ++k)
-                                if (live[k]) D[k] = min(D[k] | M[k], 1u);
+                                if (live(k, g) && M[k]) dead |= Mask(1) << k;
                         }
                         word_done = true;
                     } else {
                         const int pbit = __ffs(T) - 1;
                         ++kss;
                         cont = false;
-                        if (kss > E) {
+                        if (kss > thr()) {
                             ss_done = true;
-                            ss_count = E + 1;
                             word_done = true;
                         } else if (pbit == 31) {
                             C = 0xffffffffu;
@@ -179,7 +214,7 @@ __device__ __forceinline__ Outputs filter_pair(const PairsView &pv, int64_t p, i
                     uint32_t T = 0xffffffffu;
 #pragma unroll
                     for (int k = 0; k < NS; ++k) {
-                        if (!live[k]) continue;
+                        if (!live(k, g)) continue;
                         const uint32_t y = M[k] & C;
                         T &= (y | (0u - y));
                     }
@@ -187,20 +222,20 @@ __device__ __forceinline__ Outputs filter_pair(const PairsView &pv, int64_t p, i
                     if (T == 0u) {
                         if (w == W - 1) {
                             ss_done = true;
-                            ss_count = kss;
                         } else {
+                            Mask dd = 0u;
 #pragma unroll
                             for (int k = 0; k < NS; ++k)
-                                if (live[k]) D[k] = min(M[k] & C, 1u);
+                                if (live(k, g) && (M[k] & C)) dd |= Mask(1) << k;
+                            dead = dd;
                             cont = true;
                         }
                         break;
                     }
                     const int pbit = __ffs(T) - 1;
                     ++kss;
-                    if (kss > E) {
+                    if (kss > thr()) {
                         ss_done = true;
-                        ss_count = E + 1;
                         break;
                     }
                     if (pbit == 31) {
@@ -220,74 +255,81 @@ __device__ __forceinline__ Outputs filter_pair(const PairsView &pv, int64_t p, i
                 if constexpr (TPP > 1) hw = __shfl_sync(gmask, hw, 0, TPP);
                 h += hw;
                 if (w > 0) {
-                    uint32_t Fw = 0xffffffffu;
+                    uint32_t Fa = 0xffffffffu;
 #pragma unroll
                     for (int k = 0; k < NS; ++k) {
-                        if (!live[k]) continue;
+                        if (!live(k, g)) continue;
                         const uint32_t H = Mp[k];
                         const uint32_t l1 = __funnelshift_l(Mpp[k], H, 1);
                         const uint32_t l2 = __funnelshift_l(Mpp[k], H, 2);
                         const uint32_t r1 = __funnelshift_r(H, M[k], 1);
                         const uint32_t r2 = __funnelshift_r(H, M[k], 2);
-                        Fw &= H | (l1 & (r1 | r2)) | (l2 & r1);
+                        Fa &= H | (l1 & (r1 | r2)) | (l2 & r1);
                     }
-                    Fw = group_and<TPP>(Fw, gmask);
-                    fc += __popc(Fw);  // word w-1 is full: every bit is a column < m
-                    if (h > E && fc > E) {
-                        gk_done = true;
-                        gk_count = E + 1;
-                    }
+                    Fa = group_and<TPP>(Fa, gmask);
+                    fc += __popc(Fa);  // word w-1 is full: every bit is a column < m
+                    if (h > thr() && fc > thr()) gk_done = true;
                 }
 #pragma unroll
-                for (int k = 0; k < NS; ++k) { Mpp[k] = Mp[k]; Mp[k] = M[k]; }
+                for (int k = 0; k < NS; ++k) {
+                    if (!live(k, g)) continue;
+                    Mpp[k] = Mp[k];
+                    Mp[k] = M[k];
+                }
             }
         }
 
         Rm1 = R0;
         R0 = Rp1;
         Rp1 = load_word(pv.read, rb, w + 2, W);
+        ++w;
+        return done();
     }
 
-    if constexpr (SS) {
-        if (!ss_done) ss_count = kss;  // the snake left the grid
-    }
-    if constexpr (GK) {
-        if (!gk_done) {
+    // Counts once done(): SneakySnake's obstacles and GateKeeper's edits.
+    __device__ __forceinline__ void finish(int g, unsigned gmask, int *ss_count, int *gk_count) {
+        const int E = thr();
+        if constexpr (SS) *ss_count = imin(kss, E + 1);
+        if constexpr (GK) {
+            if (gk_done) {  // decided early: both counts exceeded E
+                *gk_count = E + 1;
+                return;
+            }
             if (W > 0) {  // amend the last word, right neighbours past the end are 0
-                uint32_t Fw = 0xffffffffu;
+                uint32_t Fa = 0xffffffffu;
 #pragma unroll
                 for (int k = 0; k < NS; ++k) {
-                    if (!live[k]) continue;
+                    if (!live(k, g)) continue;
                     const uint32_t H = Mp[k];
                     const uint32_t l1 = __funnelshift_l(Mpp[k], H, 1);
                     const uint32_t l2 = __funnelshift_l(Mpp[k], H, 2);
                     const uint32_t r1 = H >> 1;
                     const uint32_t r2 = H >> 2;
-                    Fw &= H | (l1 & (r1 | r2)) | (l2 & r1);
+                    Fa &= H | (l1 & (r1 | r2)) | (l2 & r1);
                 }
-                Fw = group_and<TPP>(Fw, gmask);
+                Fa = group_and<TPP>(Fa, gmask);
                 const uint32_t valid = (m & 31) ? ((1u << (m & 31)) - 1u) : 0xffffffffu;
-                fc += __popc(Fw & valid);
+                fc += __popc(Fa & valid);
             }
-            gk_count = (h <= E) ? h : min(fc, E + 1);
+            *gk_count = (h <= E) ? h : imin(fc, E + 1);
         }
     }
-    return Outputs{ss_count, gk_count};
-}
+};
 
 template <int DEC>
-__device__ __forceinline__ void write_outputs(const FilterArgs &a, int64_t p, int E, Outputs o) {
+__device__ __forceinline__ void write_outputs(const FilterArgs &a, int64_t p, int E, int ssc,
+                                              int gkc) {
     if constexpr (DEC == 3) {
-        a.count[p] = (int16_t)o.ss_count;
-        a.accept[p] = (uint8_t)(o.ss_count <= E);
-        a.count[a.n + p] = (int16_t)o.gk_count;
-        a.accept[a.n + p] = (uint8_t)(o.gk_count <= E);
+        a.count[p] = (int16_t)ssc;
+        a.accept[p] = (uint8_t)(ssc <= E);
+        a.count[a.n + p] = (int16_t)gkc;
+        a.accept[a.n + p] = (uint8_t)(gkc <= E);
     } else if constexpr (DEC == 1) {
-        a.count[p] = (int16_t)o.ss_count;
-        a.accept[p] = (uint8_t)(o.ss_count <= E);
+        a.count[p] = (int16_t)ssc;
+        a.accept[p] = (uint8_t)(ssc <= E);
     } else {
-        a.count[p] = (int16_t)o.gk_count;
-        a.accept[p] = (uint8_t)(o.gk_count <= E);
+        a.count[p] = (int16_t)gkc;
+        a.accept[p] = (uint8_t)(gkc <= E);
     }
 }
 
@@ -302,21 +344,35 @@ __device__ __forceinline__ void write_invalid(const FilterArgs &a, int64_t p) {
     atomicOr(a.err, ERR_PAIR_ARGS);
 }
 
-// Process pair p with the group; returns after the group wrote its outputs.
-template <int TPP, int DPT, int DEC>
-__device__ __forceinline__ void filter_group(const FilterArgs &a, int64_t p, int g,
-                                             unsigned gmask) {
-    const int m = __ldg(a.lens + p);
-    const int E = a.E ? (int)__ldg(a.E + p) : a.E_max;
-    if (m < 0 || E < 0 || E > a.E_max || E > SlotMap<TPP, DPT>::ECAP) {
+// Reads pair p's length and threshold; false (and outputs marked) if bad.
+template <int TPP, int DPT, int DEC, int XE>
+__device__ __forceinline__ bool pair_args(const FilterArgs &a, int64_t p, int g, int *m, int *E) {
+    *m = __ldg(a.lens + p);
+    *E = a.E ? (int)__ldg(a.E + p) : a.E_max;
+    if (*m < 0 || *E < 0 || *E > a.E_max || *E > SlotMap<TPP, DPT, XE>::ECAP ||
+        (XE >= 0 && *E != XE)) {
         if (g == 0) write_invalid<DEC>(a, p);
-        return;
+        return false;
     }
-    const Outputs o = filter_pair<TPP, DPT, DEC>(a.pairs, p, m, E, g, gmask);
-    if (g == 0) write_outputs<DEC>(a, p, E, o);
+    return true;
 }
 
-// The plain kernel: one thread per pair.
+// Filter pair p with the group and write its outputs.
+template <int TPP, int DPT, int DEC, int XE = -1>
+__device__ __forceinline__ void filter_group(const FilterArgs &a, int64_t p, int g,
+                                             unsigned gmask) {
+    int m, E;
+    if (!pair_args<TPP, DPT, DEC, XE>(a, p, g, &m, &E)) return;
+    PairFilter<TPP, DPT, DEC, XE> st;
+    st.init(a.pairs, p, m, E);
+    while (!st.done()) st.word(a.pairs, g, gmask);
+    int ssc = 0, gkc = 0;
+    st.finish(g, gmask, &ssc, &gkc);
+    if (g == 0) write_outputs<DEC>(a, p, E, ssc, gkc);
+}
+
+// The plain kernel: one thread per pair, every thread runs its own pair to
+// the end.
 template <int DPT, int DEC>
 __global__ void __launch_bounds__(256) filter_plain_kernel(FilterArgs a) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -325,9 +381,10 @@ __global__ void __launch_bounds__(256) filter_plain_kernel(FilterArgs a) {
 }
 
 // The batched kernel: persistent warps take chunks of `chunk` positions of
-// one bin through an atomic counter; each group of TPP lanes filters one
-// pair at a time.
-template <int TPP, int DPT, int DEC>
+// one bin through an atomic counter; the lane groups of a warp stride
+// through the chunk, one pair per group at a time, so neighbouring groups
+// read neighbouring pairs' words.
+template <int TPP, int DPT, int DEC, int XE>
 __global__ void __launch_bounds__(256) filter_batched_kernel(BatchArgs b, int bin) {
     const int lane = threadIdx.x & 31;
     const int g = lane & (TPP - 1);
@@ -337,6 +394,7 @@ __global__ void __launch_bounds__(256) filter_batched_kernel(BatchArgs b, int bi
     const int gid = lane / TPP;
     const int64_t lo = b.bin_start[bin], hi = b.bin_start[bin + 1];
     unsigned long long *counter = b.work + bin;
+    const int64_t *order = (b.order && !(b.ident && *b.ident)) ? b.order : nullptr;
     for (;;) {
         unsigned long long item = 0;
         if (lane == 0) item = atomicAdd(counter, 1ull);
@@ -345,8 +403,8 @@ __global__ void __launch_bounds__(256) filter_batched_kernel(BatchArgs b, int bi
         if (s >= hi) break;
         const int64_t e = min(hi, s + (int64_t)b.chunk);
         for (int64_t q = s + gid; q < e; q += GPW) {
-            const int64_t p = b.order ? __ldg(b.order + q) : q;
-            filter_group<TPP, DPT, DEC>(b.f, p, g, gmask);
+            const int64_t p = order ? __ldg(order + q) : q;
+            filter_group<TPP, DPT, DEC, XE>(b.f, p, g, gmask);
         }
     }
 }

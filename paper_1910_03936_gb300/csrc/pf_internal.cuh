@@ -82,6 +82,7 @@ struct BatchArgs {
     int chunk;                   // pairs per work item
     unsigned long long *work;    // work-item counter (scratch, zeroed)
     const int64_t *chunk_start;  // [nbins+1] first work item of each bin
+    const int *ident;            // device flag: order is the identity (one bin used)
 };
 
 }  // namespace pf

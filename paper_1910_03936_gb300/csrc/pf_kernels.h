@@ -9,18 +9,30 @@
 namespace pf {
 
 // One batched-filter configuration: TPP lanes per pair, DPT diagonal slots
-// per lane; it serves thresholds E <= ecap.
+// per lane; it serves thresholds E <= ecap.  xe >= 0 marks the
+// exact-threshold form (one thread per pair, serves E == xe only).
 struct KernelCfg {
-    int tpp, dpt, ecap;
+    int tpp, dpt, ecap, xe;
 };
 
 constexpr KernelCfg kBatchCfgs[] = {
-    {1, 4, 3},   {2, 4, 3},   {4, 2, 3},   {8, 1, 3},
-    {1, 8, 7},   {2, 8, 7},   {4, 4, 7},   {8, 2, 7},  {16, 1, 7},
-    {1, 16, 15}, {2, 16, 15}, {4, 8, 15},  {8, 4, 15}, {16, 2, 15}, {32, 1, 15},
-    {2, 32, 31}, {4, 16, 31}, {8, 8, 31},  {16, 4, 31}, {32, 2, 31},
+    {1, 4, 3, -1},   {2, 4, 3, -1},   {4, 2, 3, -1},   {8, 1, 3, -1},
+    {1, 8, 7, -1},   {2, 8, 7, -1},   {4, 4, 7, -1},   {8, 2, 7, -1},  {16, 1, 7, -1},
+    {1, 16, 15, -1}, {2, 16, 15, -1}, {4, 8, 15, -1},  {8, 4, 15, -1}, {16, 2, 15, -1},
+    {32, 1, 15, -1},
+    {2, 32, 31, -1}, {4, 16, 31, -1}, {8, 8, 31, -1},  {16, 4, 31, -1}, {32, 2, 31, -1},
+    {1, 1, 0, 0},    {1, 2, 1, 1},    {1, 3, 2, 2},    {1, 4, 3, 3},   {1, 5, 4, 4},
+    {1, 6, 5, 5},    {1, 7, 6, 6},    {1, 8, 7, 7},    {1, 9, 8, 8},   {1, 10, 9, 9},
+    {1, 11, 10, 10}, {1, 12, 11, 11}, {1, 13, 12, 12}, {1, 14, 13, 13}, {1, 15, 14, 14},
+    {1, 16, 15, 15},
 };
+
+// a configuration serves threshold E
+constexpr bool cfg_serves(const KernelCfg &c, int E) {
+    return c.xe >= 0 ? c.xe == E : c.ecap >= E;
+}
 constexpr int kNumBatchCfgs = sizeof(kBatchCfgs) / sizeof(kBatchCfgs[0]);
+constexpr int kFirstExactCfg = 20;  // kBatchCfgs[20 + E] serves exactly E
 
 // Plain kernel (one thread per pair): DPT = kPlainDpt[i] serves E <= DPT - 1.
 constexpr int kPlainDpt[] = {1, 2, 4, 8, 16, 32};

@@ -203,13 +203,15 @@ def test_every_batched_configuration(pf, ctx):
     from gpu_util import DevicePairs, filter_dev
     cfgs = pf.pf_kernel_configs()
     data = {}
-    for E in (0, 2, 3, 5, 7, 12, 15, 20, 31):
+    for E in (0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 20, 31):
         P = synth.generate(synth.SKEWED, 900 + E, 2500, m=150 if E < 20 else 250, E=E,
                            kmax=max(60, 3 * E))
         data[E] = (P, DevicePairs(ctx, P, fixed=int(P.lens[0])), oracle_filter(P, 3))
-    for ci, (tpp, dpt, ecap) in enumerate(cfgs):
+    for ci, (tpp, dpt, ecap, xe) in enumerate(cfgs):
         for E, (P, D, (oa, oc)) in data.items():
-            if E > ecap or E < ecap // 2 - 1:
+            if xe >= 0 and E != xe:
+                continue
+            if xe < 0 and (E > ecap or E < ecap // 2 - 1):
                 continue
             for dec in (1, 2, 3):
                 for chunk in (32, 1000):
@@ -226,7 +228,8 @@ def test_ragged_mixed_E_with_several_configs(pf, ctx, case_data):
     from gpu_util import filter_dev
     P, D, (oa, oc) = case_data["cfg3_mixed"]
     cfgs = pf.pf_kernel_configs()
-    pick = {e: next(i for i, c in enumerate(cfgs) if c[2] >= e and c[0] == (4 if e > 7 else 1))
+    pick = {e: next(i for i, c in enumerate(cfgs)
+                    if c[3] < 0 and c[2] >= e and c[0] == (4 if e > 7 else 1))
             for e in range(0, 21)}
     for e, ci in pick.items():
         pf.pf_tune_set(ctx, 3, e, ci, 128)
@@ -270,6 +273,9 @@ def test_host_checks_reject_bad_arguments(pf, ctx, case_data):
         pf.pf_filter(ctx, 4, D.pairs, D.lens, D.E, 6, acc, cnt, D.n)
     with pytest.raises(pf.PFError):
         pf.pf_tune_set(ctx, 1, 20, 0, 64)  # configuration 0 serves E <= 3
+    exact6 = [i for i, c in enumerate(pf.pf_kernel_configs()) if c[3] == 6][0]
+    with pytest.raises(pf.PFError):
+        pf.pf_tune_set(ctx, 1, 5, exact6, 64)  # serves E == 6 only
 
 
 # ---- a5 compaction ----------------------------------------------------------
@@ -358,8 +364,8 @@ def test_tuner_picks_a_valid_config_and_stays_exact(pf, ctx, case_data):
     from gpu_util import filter_dev
     P, D, (oa, oc) = case_data["cfg2_150bp_E6"]
     cfg, chunk, ms = pf.pf_tune(ctx, 3, D.pairs, D.lens, 6, reps=1)
-    tpp, dpt, ecap = pf.pf_kernel_configs()[cfg]
-    assert ecap >= 6 and ms > 0 and chunk in (64, 256, 1024)
+    tpp, dpt, ecap, xe = pf.pf_kernel_configs()[cfg]
+    assert (xe == 6 or (xe < 0 and ecap >= 6)) and ms > 0 and chunk in (64, 256, 1024)
     assert pf.pf_tune_get(ctx, 3, 6) == (cfg, chunk)
     a, c = filter_dev(ctx, D, 3)
     assert np.array_equal(c, oc) and np.array_equal(a, oa)
