@@ -245,6 +245,82 @@ PF_API pf_status pf_filter_verify(pf_ctx *ctx, unsigned deciders, const pf_pairs
                            const int32_t *lens, const int16_t *E, int E_max,
                            uint8_t *accept, int16_t *count, int32_t *dist, int64_t n);
 
+/* ---- a8: serving (continuous batching over a device-resident loop) ------ */
+
+/* The accelerator of Ch. 4 streams pairs through its filtering units and
+ * returns each decision as soon as it is made.  Here a persistent device
+ * loop takes work items (chunks of admitted requests) from a ring in
+ * mapped host memory; a host scheduler thread admits requests as slots and
+ * device memory free up, stages their bytes, publishes their items, and
+ * copies results back when the loop marks a request complete.  Requests
+ * that arrive while others run are admitted and their chunks interleave on
+ * the device.  Every device wait is bounded: the loop exits after
+ * idle_exit_us without work (the scheduler relaunches it on demand) or when
+ * stopped. */
+typedef struct {
+    size_t hbm_budget;   /* device bytes that admitted requests may hold;
+                            0 = the context's hbm_budget, else a quarter of
+                            free device memory */
+    int max_requests;    /* requests admitted at once, 1..4096 (0 = 256) */
+    int chunk_pairs;     /* pairs per work item, 32..1024 (0 = 1024) */
+    int workers;         /* blocks of the device loop (0 = 2 per SM) */
+    int idle_exit_us;    /* the device loop ends after this long without
+                            work, 50..10^6 (0 = 500) */
+    int start_paused;    /* nonzero: admit and stage, but run nothing until
+                            pf_serve_resume */
+} pf_serve_config;
+
+/* One request: n pairs in HOST memory.  Pair p is reads[byte_off[p] ..
+ * byte_off[p+1]) against refs[byte_off[p] .. byte_off[p+1]).  All buffers
+ * belong to the caller and must stay valid until pf_wait/pf_poll reports
+ * the request done.  Outputs as in pf_filter_verify: accept and count
+ * [slots*n], dist [n] = min(ED, E+1) for pairs the first selected decider
+ * accepts, E+1 for the others. */
+typedef struct {
+    unsigned deciders;
+    int64_t n;
+    const uint8_t *reads;
+    const uint8_t *refs;
+    const int64_t *byte_off;   /* host int64[n+1], non-decreasing */
+    const int16_t *E;          /* host int16[n], each 0..PF_MAX_E */
+    uint8_t *accept;
+    int16_t *count;
+    int32_t *dist;
+} pf_request;
+
+typedef struct {
+    uint64_t submitted, completed, failed, pairs_completed;
+    uint64_t loop_launches;    /* times the device loop was (re)started */
+} pf_serve_stats;
+
+/* Start serving on ctx (PF_EBUSY if already serving).  Allocates the
+ * request arena, the ring and the scheduler thread. */
+PF_API pf_status pf_serve_start(pf_ctx *ctx, const pf_serve_config *cfg);
+
+/* Queue a request; *ticket identifies it.  Malformed requests (null
+ * pointers, decreasing offsets, E outside [0, PF_MAX_E]) return PF_EINVAL,
+ * requests that could never fit the budget PF_ENOMEM; neither is queued. */
+PF_API pf_status pf_submit(pf_ctx *ctx, const pf_request *req, uint64_t *ticket);
+
+/* *done = 1 once the request's results are in its host buffers. */
+PF_API pf_status pf_poll(pf_ctx *ctx, uint64_t ticket, int *done);
+
+/* Wait up to timeout_ms (< 0: no limit) for the request.  Returns its
+ * status (PF_OK, PF_EINVAL for pairs the device found invalid,
+ * PF_ECANCELLED if serving stopped first) or PF_ETIMEOUT if it is still in
+ * flight; *latency_ms (may be NULL) = submit to results in host memory.  A
+ * finished ticket is released by the first pf_wait that reports it. */
+PF_API pf_status pf_wait(pf_ctx *ctx, uint64_t ticket, int timeout_ms, double *latency_ms);
+
+/* Run a loop started with start_paused. */
+PF_API pf_status pf_serve_resume(pf_ctx *ctx);
+
+PF_API pf_status pf_serve_stats_get(pf_ctx *ctx, pf_serve_stats *out);
+
+/* Stop the device loop and the scheduler; requests not finished end with
+ * PF_ECANCELLED. */
+PF_API pf_status pf_serve_stop(pf_ctx *ctx);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,6 +20,8 @@ __all__ = [
     "pf_pack_layout", "pf_pack", "pf_pack_fixed", "pf_filter", "pf_filter_plain",
     "pf_compact", "pf_verify", "pf_filter_verify", "library_path", "load", "pack_pairs",
     "pf_kernel_configs", "pf_tune_set", "pf_tune_get", "pf_tune", "pf_compact_noalloc",
+    "ServeConfig", "Request", "pf_serve_start", "pf_submit", "pf_poll", "pf_wait",
+    "pf_serve_resume", "pf_serve_stats_get", "pf_serve_stop",
 ]
 
 PF_SNEAKYSNAKE = 1
@@ -48,6 +50,26 @@ class _Seqs(ctypes.Structure):
 
 class _Pairs(ctypes.Structure):
     _fields_ = [("read", _Seqs), ("ref", _Seqs)]
+
+
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("max_requests", ctypes.c_int),
+                ("chunk_pairs", ctypes.c_int), ("workers", ctypes.c_int),
+                ("idle_exit_us", ctypes.c_int), ("start_paused", ctypes.c_int)]
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("deciders", ctypes.c_uint), ("n", ctypes.c_int64),
+                ("reads", ctypes.c_void_p), ("refs", ctypes.c_void_p),
+                ("byte_off", ctypes.c_void_p), ("E", ctypes.c_void_p),
+                ("accept", ctypes.c_void_p), ("count", ctypes.c_void_p),
+                ("dist", ctypes.c_void_p)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("failed", ctypes.c_uint64), ("pairs_completed", ctypes.c_uint64),
+                ("loop_launches", ctypes.c_uint64)]
 
 
 _lib = None
@@ -83,6 +105,13 @@ def load():
         "pf_verify": [P, ctypes.POINTER(_Pairs), P, P, I, P, P, I64, P],
         "pf_filter_verify": [P, U, ctypes.POINTER(_Pairs), P, P, I, P, P, P, I64],
         "pf_kernel_configs": [P, P, P, P, I, ctypes.POINTER(ctypes.c_int)],
+        "pf_serve_start": [P, ctypes.POINTER(ServeConfig)],
+        "pf_submit": [P, ctypes.POINTER(_Request), ctypes.POINTER(ctypes.c_uint64)],
+        "pf_poll": [P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)],
+        "pf_wait": [P, ctypes.c_uint64, I, ctypes.POINTER(ctypes.c_double)],
+        "pf_serve_resume": [P],
+        "pf_serve_stats_get": [P, ctypes.POINTER(ServeStats)],
+        "pf_serve_stop": [P],
         "pf_tune_set": [P, U, I, I, I],
         "pf_tune_get": [P, U, I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
         "pf_tune": [P, U, ctypes.POINTER(_Pairs), P, I, I64, I, ctypes.POINTER(ctypes.c_int),
@@ -367,3 +396,72 @@ def pf_tune(ctx, deciders, pairs, lens, E, n=None, reps=3):
                           int(reps), ctypes.byref(c), ctypes.byref(k), ctypes.byref(ms)),
            ctx.handle)
     return c.value, k.value, ms.value
+
+
+# ---- a8 serving -----------------------------------------------------------
+
+def pf_serve_start(ctx, hbm_budget=0, max_requests=0, chunk_pairs=0, workers=0,
+                   idle_exit_us=0, start_paused=False):
+    cfg = ServeConfig(hbm_budget, max_requests, chunk_pairs, workers, idle_exit_us,
+                      1 if start_paused else 0)
+    _check(load().pf_serve_start(ctx.handle, ctypes.byref(cfg)), ctx.handle)
+
+
+class Request:
+    """A request in host memory (numpy arrays).  The arrays are kept
+    referenced here until the request is waited for."""
+
+    def __init__(self, deciders, reads, refs, byte_off, E):
+        import numpy as np
+        self.reads = np.ascontiguousarray(reads, dtype=np.uint8)
+        self.refs = np.ascontiguousarray(refs, dtype=np.uint8)
+        self.byte_off = np.ascontiguousarray(byte_off, dtype=np.int64)
+        self.E = np.ascontiguousarray(E, dtype=np.int16)
+        self.n = len(self.byte_off) - 1
+        slots = 2 if deciders == 3 else 1
+        self.deciders = deciders
+        self.accept = np.zeros(slots * max(self.n, 1), dtype=np.uint8)
+        self.count = np.zeros(slots * max(self.n, 1), dtype=np.int16)
+        self.dist = np.zeros(max(self.n, 1), dtype=np.int32)
+        self.ticket = None
+
+    def _c(self):
+        ptr = lambda a: ctypes.c_void_p(a.ctypes.data) if a.size else None
+        return _Request(self.deciders, self.n, ptr(self.reads), ptr(self.refs),
+                        ptr(self.byte_off), ptr(self.E), ptr(self.accept),
+                        ptr(self.count), ptr(self.dist))
+
+
+def pf_submit(ctx, req):
+    t = ctypes.c_uint64()
+    c = req._c()
+    _check(load().pf_submit(ctx.handle, ctypes.byref(c), ctypes.byref(t)), ctx.handle)
+    req.ticket = t.value
+    return t.value
+
+
+def pf_poll(ctx, ticket):
+    d = ctypes.c_int()
+    _check(load().pf_poll(ctx.handle, ticket, ctypes.byref(d)), ctx.handle)
+    return bool(d.value)
+
+
+def pf_wait(ctx, ticket, timeout_ms=-1):
+    """Returns (status, latency_ms); status 0 is PF_OK, 4 PF_ETIMEOUT."""
+    lat = ctypes.c_double()
+    st = load().pf_wait(ctx.handle, ticket, int(timeout_ms), ctypes.byref(lat))
+    return st, lat.value
+
+
+def pf_serve_resume(ctx):
+    _check(load().pf_serve_resume(ctx.handle), ctx.handle)
+
+
+def pf_serve_stats_get(ctx):
+    st = ServeStats()
+    _check(load().pf_serve_stats_get(ctx.handle, ctypes.byref(st)), ctx.handle)
+    return {f: getattr(st, f) for f, _ in ServeStats._fields_}
+
+
+def pf_serve_stop(ctx):
+    _check(load().pf_serve_stop(ctx.handle), ctx.handle)

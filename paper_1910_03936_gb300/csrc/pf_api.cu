@@ -115,8 +115,6 @@ dist_fill_rejected_kernel(const uint8_t *accept, const int16_t *E, int E_max, in
 
 static thread_local std::string g_tls_msg;
 
-void pf_serve_teardown(pf_ctx *) {}
-
 pf_status pf_ctx::fail(pf_status s, const char *fmt, ...) {
     char buf[512];
     va_list ap;

@@ -77,7 +77,7 @@ __device__ __forceinline__ int imin(int a, int b) { return a < b ? a : b; }
 // processes one reference word and reports whether both deciders are
 // decided, finish() closes GateKeeper's last word.  Every lane of the
 // group holds the same copy of the scalar state.
-template <int TPP, int DPT, int DEC, int XE = -1>
+template <int TPP, int DPT, int DEC, int XE = -1, typename L = LdNC>
 struct PairFilter {
     using SM = SlotMap<TPP, DPT, XE>;
     static constexpr int NS = SM::NS;
@@ -114,12 +114,12 @@ struct PairFilter {
         E = E_;
         W = (m + 31) >> 5;
         w = 0;
-        rb = pv.read.start(p);
-        fb = pv.ref.start(p);
-        Rm1 = load_word(pv.read, rb, -1, W);
-        R0 = load_word(pv.read, rb, 0, W);
-        Rp1 = load_word(pv.read, rb, 1, W);
-        Fw = load_word(pv.ref, fb, 0, W);
+        rb = pv.read.template start<L>(p);
+        fb = pv.ref.template start<L>(p);
+        Rm1 = load_word<L>(pv.read, rb, -1, W);
+        R0 = load_word<L>(pv.read, rb, 0, W);
+        Rp1 = load_word<L>(pv.read, rb, 1, W);
+        Fw = load_word<L>(pv.ref, fb, 0, W);
 #pragma unroll
         for (int k = 0; k < NS; ++k) { Mp[k] = 0u; Mpp[k] = 0u; }
         dead = 0u;
@@ -137,7 +137,7 @@ struct PairFilter {
     // Process reference word w; returns done().
     __device__ __forceinline__ bool word(const PairsView &pv, int g, unsigned gmask) {
         const Word3 F = Fw;
-        Fw = load_word(pv.ref, fb, w + 1, W);  // prefetch the next reference word
+        Fw = load_word<L>(pv.ref, fb, w + 1, W);  // prefetch the next reference word
         uint32_t M[NS];
         const uint32_t valid =
             (w == W - 1 && (m & 31)) ? ((1u << (m & 31)) - 1u) : 0xffffffffu;
@@ -281,7 +281,7 @@ struct PairFilter {
 
         Rm1 = R0;
         R0 = Rp1;
-        Rp1 = load_word(pv.read, rb, w + 2, W);
+        Rp1 = load_word<L>(pv.read, rb, w + 2, W);
         ++w;
         return done();
     }

@@ -15,13 +15,28 @@ enum : unsigned {
     ERR_TIMEOUT = 4u,     // a bounded device wait ran out
 };
 
+// Load policies.  LdNC: read-only data cache (data that no kernel writes
+// while the reader runs).  LdCG: L2 only, for data that a long-running
+// kernel reads after it was written during its lifetime (copy-engine
+// uploads, words the same block just produced), where an L1 or read-only
+// cache line from earlier could be stale.
+struct LdNC {
+    template <typename T>
+    static __device__ __forceinline__ T ld(const T *p) { return __ldg(p); }
+};
+struct LdCG {
+    template <typename T>
+    static __device__ __forceinline__ T ld(const T *p) { return __ldcg(p); }
+};
+
 // Plain-old-data view of one set of packed sequences, passed by value.
 struct SeqView {
     const uint32_t *lo, *hi, *nm;
     const int64_t *off;   // per-sequence first word, or null
     int64_t stride;       // words per sequence when off is null
+    template <typename L = LdNC>
     __device__ __forceinline__ int64_t start(int64_t s) const {
-        return off ? __ldg(off + s) : s * stride;
+        return off ? L::ld(off + s) : s * stride;
     }
 };
 
@@ -34,12 +49,13 @@ struct Word3 {
     uint32_t lo, hi, nm;
 };
 
+template <typename L = LdNC>
 __device__ __forceinline__ Word3 load_word(const SeqView &v, int64_t base, int q, int W) {
     Word3 r;
     if (q >= 0 && q < W) {
-        r.lo = __ldg(v.lo + base + q);
-        r.hi = __ldg(v.hi + base + q);
-        r.nm = __ldg(v.nm + base + q);
+        r.lo = L::ld(v.lo + base + q);
+        r.hi = L::ld(v.hi + base + q);
+        r.nm = L::ld(v.nm + base + q);
     } else {
         r.lo = 0u; r.hi = 0u; r.nm = 0xffffffffu;
     }

@@ -63,6 +63,7 @@ __device__ __forceinline__ void slow_word(const uint32_t *vals, int vb, uint32_t
 }
 
 // Pack word w of a sequence whose bytes start at `src` (len bytes).
+template <typename L = LdNC>
 __device__ __forceinline__ void pack_word(const uint8_t *src, int len, int w, uint32_t *lo,
                                           uint32_t *hi, uint32_t *nm, unsigned *err) {
     const int b0 = 32 * w;
@@ -75,7 +76,7 @@ __device__ __forceinline__ void pack_word(const uint8_t *src, int len, int w, ui
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         const uintptr_t wa = reinterpret_cast<uintptr_t>(aw + k);
-        u[k] = (wa < end) ? __ldg(aw + k) : 0u;
+        u[k] = (wa < end) ? L::ld(aw + k) : 0u;
     }
     uint32_t v[8];
     uint32_t olo = 0u, ohi = 0u, onm = 0u, bad = 0u;

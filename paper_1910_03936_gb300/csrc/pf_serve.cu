@@ -1,0 +1,727 @@
+// a8: serving.  A persistent device loop takes work items (chunks of
+// admitted requests) from a ring in mapped host memory; a host scheduler
+// thread admits requests by slots, device memory and ring room, stages
+// them, publishes their items and returns results.  Contracts: pf.h.
+//
+// Every device wait is bounded: a block that finds no item sleeps in
+// short steps and leaves after idle_exit_us (globaltimer) or when the stop
+// flag is set; the scheduler relaunches the loop when new items appear.
+// Items are claimed by compare-and-swap on a device head counter only
+// after the block has seen them published, so an exiting block never
+// drops an item.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "pf_ctx.h"
+#include "pf_filter.cuh"
+#include "pf_pack.cuh"
+#include "pf_verify.cuh"
+
+namespace pf {
+
+constexpr int kServeThreads = 256;
+constexpr int kServeMaxChunk = 1024;
+constexpr int kServeTpp = 8;      // lanes per pair in the loop's filter
+constexpr int kServeDpt = 8;      // slots per lane: E <= 31
+constexpr uint64_t kRingSize = 1u << 16;
+
+// Per-slot request descriptor, in device memory (uploaded with the request).
+struct ServeDesc {
+    const uint8_t *reads, *refs;
+    const int64_t *byte_off, *word_off;
+    const int16_t *E;
+    uint32_t *rlo, *rhi, *rnm, *flo, *fhi, *fnm;
+    uint8_t *accept;
+    int16_t *count;
+    int32_t *dist;
+    unsigned *err;
+    int64_t n;
+    int chunk, nchunks;
+    unsigned deciders;
+    unsigned epoch;
+};
+
+struct ServeDevice {
+    const ServeDesc *desc;            // [max_requests], device
+    unsigned *done;                   // [max_requests], device: chunks finished
+    unsigned long long *head;         // device: next item to claim
+    const unsigned long long *items;  // mapped host ring
+    const unsigned long long *tail;   // mapped host: items published
+    const unsigned *stop;             // mapped host
+    unsigned *complete;               // mapped host [max_requests]: epoch of the finished request
+    unsigned long long idle_ns;
+};
+
+__device__ __forceinline__ unsigned long long ld_acquire_sys(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned ld_relaxed_sys(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.relaxed.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_sys64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_sys(unsigned *p, unsigned v) {
+    asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// The descriptor of a slot, read through L2: the copy engine rewrites it for
+// every request admitted to the slot while the loop runs.
+__device__ __forceinline__ ServeDesc load_desc(const ServeDesc *p) {
+    static_assert(sizeof(ServeDesc) % 8 == 0, "descriptor is read in 8-byte words");
+    ServeDesc d;
+    const unsigned long long *src = reinterpret_cast<const unsigned long long *>(p);
+    unsigned long long *dst = reinterpret_cast<unsigned long long *>(&d);
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(ServeDesc) / 8); ++i) dst[i] = __ldcg(src + i);
+    return d;
+}
+
+template <int DEC>
+__device__ __forceinline__ void serve_filter_chunk(const ServeDesc &d, const PairsView &pv,
+                                                   int64_t c0, int64_t c1) {
+    const int lane = threadIdx.x & 31;
+    const int g = lane & (kServeTpp - 1);
+    const unsigned gmask = ((1u << kServeTpp) - 1u) << (lane & ~(kServeTpp - 1));
+    const int group = threadIdx.x / kServeTpp;
+    constexpr int groups = kServeThreads / kServeTpp;
+    FilterArgs a;
+    a.pairs = pv;
+    a.accept = d.accept;
+    a.count = d.count;
+    a.n = d.n;
+    for (int64_t p = c0 + group; p < c1; p += groups) {
+        const int64_t b0 = __ldcg(d.byte_off + p);
+        const int m = (int)(__ldcg(d.byte_off + p + 1) - b0);
+        const int E = __ldcg(d.E + p);
+        if (m < 0 || E < 0 || E > PF_MAX_E) {
+            if (g == 0) {
+                a.count[p] = -1;
+                a.accept[p] = 0;
+                if (DEC == 3) {
+                    a.count[a.n + p] = -1;
+                    a.accept[a.n + p] = 0;
+                }
+                atomicOr(d.err, ERR_PAIR_ARGS);
+            }
+            continue;
+        }
+        PairFilter<kServeTpp, kServeDpt, DEC, -1, LdCG> st;
+        st.init(pv, p, m, E);
+        while (!st.done()) st.word(pv, g, gmask);
+        int ssc = 0, gkc = 0;
+        st.finish(g, gmask, &ssc, &gkc);
+        if (g == 0) write_outputs<DEC>(a, p, E, ssc, gkc);
+    }
+}
+
+__global__ void __launch_bounds__(kServeThreads) serve_loop_kernel(ServeDevice sd) {
+    __shared__ unsigned long long s_item;
+    __shared__ int s_cmd;
+    __shared__ int64_t s_woff[kServeMaxChunk + 1];
+    __shared__ int64_t s_boff[kServeMaxChunk + 1];
+    unsigned long long last_work = globaltimer_ns();
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int cmd = 0;
+            for (unsigned polls = 0;; ++polls) {
+                if (ld_relaxed_sys(sd.stop)) break;
+                const unsigned long long t = ld_acquire_sys(sd.tail);
+                const unsigned long long h = *(volatile unsigned long long *)sd.head;
+                if (h < t) {
+                    if (atomicCAS(sd.head, h, h + 1) == h) {
+                        s_item = ld_relaxed_sys64(sd.items + (h % kRingSize));
+                        cmd = 1;
+                        break;
+                    }
+                    continue;  // another block took it: look again at once
+                }
+                const unsigned long long now = globaltimer_ns();
+                if (now - last_work > sd.idle_ns || polls > (1u << 26)) break;
+                __nanosleep(2000);
+            }
+            s_cmd = cmd;
+        }
+        __syncthreads();
+        if (s_cmd == 0) return;
+        const unsigned long long item = s_item;
+        const int slot = (int)(item >> 32);
+        const int ci = (int)(item & 0xffffffffu);
+        const ServeDesc d = load_desc(sd.desc + slot);  // uploaded before the item was published
+        const int64_t c0 = (int64_t)ci * d.chunk;
+        const int64_t c1 = min(d.n, c0 + (int64_t)d.chunk);
+        const int np = (int)(c1 - c0);
+
+        // ---- pack the chunk's reads and references (a1)
+        for (int i = threadIdx.x; i <= np; i += blockDim.x) {
+            s_woff[i] = __ldcg(d.word_off + c0 + i);
+            s_boff[i] = __ldcg(d.byte_off + c0 + i);
+        }
+        __syncthreads();
+        const int64_t wbase = s_woff[0];
+        const int wtot = (int)(s_woff[np] - wbase);
+        for (int j = threadIdx.x; j < wtot; j += blockDim.x) {
+            const int64_t gw = wbase + j;
+            int l = 0, r = np - 1;
+            while (l < r) {
+                const int mid = (l + r + 1) >> 1;
+                if (s_woff[mid] <= gw) l = mid; else r = mid - 1;
+            }
+            const int w = (int)(gw - s_woff[l]);
+            const int len = (int)(s_boff[l + 1] - s_boff[l]);
+            pack_word<LdCG>(d.reads + s_boff[l], len, w, d.rlo + gw, d.rhi + gw, d.rnm + gw, d.err);
+            pack_word<LdCG>(d.refs + s_boff[l], len, w, d.flo + gw, d.fhi + gw, d.fnm + gw, d.err);
+        }
+        __syncthreads();
+
+        // ---- filter (a2-a4)
+        PairsView pv;
+        pv.read = SeqView{d.rlo, d.rhi, d.rnm, d.word_off, 0};
+        pv.ref = SeqView{d.flo, d.fhi, d.fnm, d.word_off, 0};
+        if (d.deciders == 1u) serve_filter_chunk<1>(d, pv, c0, c1);
+        else if (d.deciders == 2u) serve_filter_chunk<2>(d, pv, c0, c1);
+        else serve_filter_chunk<3>(d, pv, c0, c1);
+        __syncthreads();
+
+        // ---- verify the accepted pairs (a5-a6); the first selected
+        // decider's flags are slot 0
+        for (int64_t p = c0 + threadIdx.x; p < c1; p += blockDim.x) {
+            const int E = __ldcg(d.E + p);
+            const int m = (int)(s_boff[p - c0 + 1] - s_boff[p - c0]);
+            int32_t v;
+            if (m < 0 || E < 0 || E > PF_MAX_E) v = -1;
+            else if (__ldcg(d.accept + p)) v = verify_pair<uint64_t, LdCG>(pv, p, m, E);
+            else v = E + 1;
+            d.dist[p] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const unsigned prev = atomicAdd(sd.done + slot, 1u);
+            if (prev + 1 == (unsigned)d.nchunks) {
+                __threadfence_system();
+                st_release_sys(sd.complete + slot, d.epoch);
+            }
+        }
+        last_work = globaltimer_ns();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+
+struct ServeReq {
+    uint64_t ticket = 0;
+    pf_request req{};
+    int slot = -1;
+    size_t off = 0, bytes = 0;
+    int64_t total_bytes = 0, total_words = 0;
+    int nchunks = 0;
+    unsigned epoch = 0;
+    enum State { PENDING, STAGING, RUNNING, DRAINING, DONE } state = PENDING;
+    cudaEvent_t ev = nullptr;
+    std::chrono::steady_clock::time_point t_submit, t_done;
+    pf_status status = PF_OK;
+    unsigned *h_err = nullptr;  // pinned, per slot
+};
+
+struct ServeState {
+    pf_serve_config cfg{};
+    int device = 0;
+    size_t budget = 0;
+    char *arena = nullptr;
+    std::map<size_t, size_t> free_list;  // offset -> size
+    ServeDesc *d_desc = nullptr;
+    ServeDesc *h_desc = nullptr;         // pinned staging, one per slot
+    unsigned *d_done = nullptr;
+    unsigned long long *d_head = nullptr;
+    unsigned long long *h_items = nullptr, *h_tail = nullptr;
+    unsigned *h_stop = nullptr, *h_complete = nullptr, *h_errs = nullptr;
+    ServeDevice dev{};
+    cudaStream_t s_copy = nullptr, s_loop = nullptr;
+    cudaEvent_t ev_loop = nullptr;
+    bool loop_running = false;
+    std::atomic<bool> paused{false};
+    uint64_t published = 0;   // items published (host copy of *h_tail)
+    uint64_t inflight_items = 0;
+
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done, cv_idle;
+    bool quit = false;
+    int waiters = 0;      // threads inside pf_wait
+    std::thread th;
+    uint64_t next_ticket = 1;
+    std::deque<std::shared_ptr<ServeReq>> pending;
+    std::map<uint64_t, std::shared_ptr<ServeReq>> reqs;
+    std::vector<int> free_slots;
+    std::vector<unsigned> slot_epoch;
+    pf_serve_stats stats{};
+    std::string fatal;
+
+    bool alloc(size_t bytes, size_t *off) {
+        for (auto it = free_list.begin(); it != free_list.end(); ++it) {
+            if (it->second >= bytes) {
+                *off = it->first;
+                const size_t rest = it->second - bytes;
+                const size_t o = it->first + bytes;
+                free_list.erase(it);
+                if (rest) free_list[o] = rest;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes) {
+        auto it = free_list.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_list.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_list.erase(nx);
+        }
+        if (it != free_list.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_list.erase(it);
+            }
+        }
+    }
+};
+
+namespace {
+
+inline size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Device bytes a request needs in the arena.
+size_t request_bytes(const pf_request &r, int64_t total_bytes, int64_t total_words) {
+    const int slots = (r.deciders == 3u) ? 2 : 1;
+    const size_t n = (size_t)r.n;
+    return up256((size_t)total_bytes) * 2 + up256((n + 1) * 8) * 2 + up256(n * 2) +
+           up256((size_t)total_words * 4) * 6 + up256(slots * n) + up256(slots * n * 2) +
+           up256(n * 4) + 256;
+}
+
+void stage(pf_ctx *ctx, ServeState &S, ServeReq &q) {
+    const pf_request &r = q.req;
+    char *b = S.arena + q.off;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        char *p = b + o;
+        o += up256(bytes);
+        return p;
+    };
+    const int slots = (r.deciders == 3u) ? 2 : 1;
+    const size_t n = (size_t)r.n;
+    ServeDesc &d = S.h_desc[q.slot];
+    d.reads = reinterpret_cast<uint8_t *>(take((size_t)q.total_bytes));
+    d.refs = reinterpret_cast<uint8_t *>(take((size_t)q.total_bytes));
+    int64_t *boff = reinterpret_cast<int64_t *>(take((n + 1) * 8));
+    int64_t *woff = reinterpret_cast<int64_t *>(take((n + 1) * 8));
+    d.byte_off = boff;
+    d.word_off = woff;
+    d.E = reinterpret_cast<int16_t *>(take(n * 2));
+    uint32_t *pl[6];
+    for (auto &x : pl) x = reinterpret_cast<uint32_t *>(take((size_t)q.total_words * 4));
+    d.rlo = pl[0]; d.rhi = pl[1]; d.rnm = pl[2];
+    d.flo = pl[3]; d.fhi = pl[4]; d.fnm = pl[5];
+    d.accept = reinterpret_cast<uint8_t *>(take(slots * n));
+    d.count = reinterpret_cast<int16_t *>(take(slots * n * 2));
+    d.dist = reinterpret_cast<int32_t *>(take(n * 4));
+    d.err = reinterpret_cast<unsigned *>(take(4));
+    d.n = r.n;
+    d.chunk = S.cfg.chunk_pairs;
+    d.nchunks = q.nchunks;
+    d.deciders = r.deciders;
+    d.epoch = q.epoch;
+
+    // host-side offsets: rebased bytes and word starts
+    std::vector<int64_t> hb(n + 1), hw(n + 1);
+    int64_t acc = 0;
+    for (size_t p = 0; p <= n; ++p) {
+        hb[p] = r.byte_off[p] - r.byte_off[0];
+        hw[p] = acc;
+        if (p < n) acc += (r.byte_off[p + 1] - r.byte_off[p] + 31) / 32;
+    }
+    cudaStream_t st = S.s_copy;
+    const uint8_t *src_r = r.reads + r.byte_off[0];
+    const uint8_t *src_f = r.refs + r.byte_off[0];
+    if (q.total_bytes) {
+        cudaMemcpyAsync((void *)d.reads, src_r, (size_t)q.total_bytes, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync((void *)d.refs, src_f, (size_t)q.total_bytes, cudaMemcpyHostToDevice, st);
+    }
+    cudaMemcpyAsync(boff, hb.data(), (n + 1) * 8, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(woff, hw.data(), (n + 1) * 8, cudaMemcpyHostToDevice, st);
+    if (n) cudaMemcpyAsync((void *)d.E, r.E, n * 2, cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(d.err, 0, 4, st);
+    cudaMemsetAsync(S.d_done + q.slot, 0, sizeof(unsigned), st);
+    cudaMemcpyAsync(S.d_desc + q.slot, &d, sizeof(ServeDesc), cudaMemcpyHostToDevice, st);
+    cudaEventRecord(q.ev, st);
+    (void)ctx;
+}
+
+void drain(ServeState &S, ServeReq &q) {
+    const pf_request &r = q.req;
+    const ServeDesc &d = S.h_desc[q.slot];
+    const int slots = (r.deciders == 3u) ? 2 : 1;
+    const size_t n = (size_t)r.n;
+    cudaStream_t st = S.s_copy;
+    if (n) {
+        cudaMemcpyAsync(r.accept, d.accept, slots * n, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(r.count, d.count, slots * n * 2, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(r.dist, d.dist, n * 4, cudaMemcpyDeviceToHost, st);
+    }
+    cudaMemcpyAsync(S.h_errs + q.slot, d.err, 4, cudaMemcpyDeviceToHost, st);
+    cudaEventRecord(q.ev, st);
+}
+
+void finish_req(ServeState &S, ServeReq &q, pf_status st) {
+    q.status = st;
+    q.state = ServeReq::DONE;
+    q.t_done = std::chrono::steady_clock::now();
+    if (q.slot >= 0) {
+        S.free_slots.push_back(q.slot);
+        S.release(q.off, q.bytes);
+        S.inflight_items -= (uint64_t)q.nchunks;
+        q.slot = -1;
+    }
+    if (st == PF_OK) {
+        S.stats.completed++;
+        S.stats.pairs_completed += (uint64_t)q.req.n;
+    } else {
+        S.stats.failed++;
+    }
+}
+
+void scheduler(pf_ctx *ctx, ServeState *Sp) {
+    ServeState &S = *Sp;
+    cudaSetDevice(S.device);
+    std::unique_lock<std::mutex> lk(S.mu);
+    while (!S.quit) {
+        bool progress = false;
+        // admission: FIFO, as slots, device memory and ring room allow
+        while (!S.pending.empty() && !S.free_slots.empty()) {
+            auto q = S.pending.front();
+            if (S.inflight_items + (uint64_t)q->nchunks > kRingSize) break;
+            size_t off = 0;
+            if (!S.alloc(q->bytes, &off)) break;
+            S.pending.pop_front();
+            q->off = off;
+            q->slot = S.free_slots.back();
+            S.free_slots.pop_back();
+            q->epoch = ++S.slot_epoch[q->slot];
+            S.inflight_items += (uint64_t)q->nchunks;
+            q->state = ServeReq::STAGING;
+            stage(ctx, S, *q);
+            progress = true;
+        }
+        for (auto &kv : S.reqs) {
+            ServeReq &q = *kv.second;
+            if (q.state == ServeReq::STAGING && cudaEventQuery(q.ev) == cudaSuccess) {
+                // publish the request's items, then the new tail
+                for (int c = 0; c < q.nchunks; ++c)
+                    S.h_items[(S.published + c) % kRingSize] =
+                        ((unsigned long long)q.slot << 32) | (unsigned)c;
+                S.published += (uint64_t)q.nchunks;
+                std::atomic_thread_fence(std::memory_order_release);
+                *(volatile unsigned long long *)S.h_tail = S.published;
+                q.state = ServeReq::RUNNING;
+                if (q.nchunks == 0) {
+                    q.state = ServeReq::DRAINING;
+                    drain(S, q);
+                }
+                progress = true;
+            } else if (q.state == ServeReq::RUNNING &&
+                       *(volatile unsigned *)(S.h_complete + q.slot) == q.epoch) {
+                std::atomic_thread_fence(std::memory_order_acquire);
+                q.state = ServeReq::DRAINING;
+                drain(S, q);
+                progress = true;
+            } else if (q.state == ServeReq::DRAINING && cudaEventQuery(q.ev) == cudaSuccess) {
+                const unsigned e = S.h_errs[q.slot];
+                finish_req(S, q, (e & ERR_PAIR_ARGS) ? PF_EINVAL : (e & ERR_BYTES) ? PF_EDATA : PF_OK);
+                S.cv_done.notify_all();
+                progress = true;
+            }
+        }
+        // the device loop: (re)start it while published items wait
+        if (S.loop_running && cudaEventQuery(S.ev_loop) == cudaSuccess) S.loop_running = false;
+        bool waiting = false;
+        for (auto &kv : S.reqs)
+            if (kv.second->state == ServeReq::RUNNING) waiting = true;
+        if (waiting && !S.loop_running && !S.paused.load()) {
+            serve_loop_kernel<<<S.cfg.workers, kServeThreads, 0, S.s_loop>>>(S.dev);
+            if (cudaGetLastError() != cudaSuccess) {
+                S.fatal = "serve loop launch failed";
+            } else {
+                cudaEventRecord(S.ev_loop, S.s_loop);
+                S.loop_running = true;
+                S.stats.loop_launches++;
+            }
+        }
+        bool busy = !S.pending.empty();
+        for (auto &kv : S.reqs)
+            if (kv.second->state != ServeReq::DONE) busy = true;
+        if (!progress) {
+            if (busy) {
+                lk.unlock();
+                std::this_thread::sleep_for(std::chrono::microseconds(20));
+                lk.lock();
+            } else {
+                S.cv_work.wait_for(lk, std::chrono::milliseconds(20));
+            }
+        }
+    }
+}
+
+}  // namespace
+
+}  // namespace pf
+
+using namespace pf;
+
+void pf_serve_teardown(pf_ctx *ctx) {
+    if (ctx && ctx->serve) pf_serve_stop(ctx);
+}
+
+extern "C" {
+
+pf_status pf_serve_start(pf_ctx *ctx, const pf_serve_config *cfg) {
+    if (!ctx) return PF_EINVAL;
+    if (ctx->serve) return ctx->fail(PF_EBUSY, "already serving");
+    if (!cfg) return ctx->fail(PF_EINVAL, "null config");
+    pf_serve_config c = *cfg;
+    if (c.max_requests == 0) c.max_requests = 256;
+    if (c.chunk_pairs == 0) c.chunk_pairs = kServeMaxChunk;
+    if (c.idle_exit_us == 0) c.idle_exit_us = 500;
+    if (c.max_requests < 1 || c.max_requests > 4096 || c.chunk_pairs < 32 ||
+        c.chunk_pairs > kServeMaxChunk || c.idle_exit_us < 50 || c.idle_exit_us > 1000000 ||
+        c.workers < 0)
+        return ctx->fail(PF_EINVAL, "serve config out of range");
+    cudaSetDevice(ctx->device);
+    if (c.workers == 0) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_loop_kernel, kServeThreads, 0);
+        c.workers = std::max(1, std::min(per_sm, 2)) * ctx->sms;
+    }
+    size_t budget = c.hbm_budget ? c.hbm_budget : ctx->hbm_budget;
+    if (!budget) {
+        size_t fr = 0, tot = 0;
+        cudaMemGetInfo(&fr, &tot);
+        budget = fr / 4;
+    }
+    budget &= ~size_t(255);
+    auto S = new ServeState();
+    S->cfg = c;
+    S->device = ctx->device;
+    S->budget = budget;
+    S->paused = c.start_paused != 0;
+    bool ok = cudaMalloc(&S->arena, budget) == cudaSuccess &&
+              cudaMalloc(&S->d_desc, sizeof(ServeDesc) * c.max_requests) == cudaSuccess &&
+              cudaMalloc(&S->d_done, sizeof(unsigned) * c.max_requests) == cudaSuccess &&
+              cudaMalloc(&S->d_head, sizeof(unsigned long long)) == cudaSuccess &&
+              cudaMemset(S->d_head, 0, sizeof(unsigned long long)) == cudaSuccess &&
+              cudaHostAlloc(&S->h_desc, sizeof(ServeDesc) * c.max_requests, 0) == cudaSuccess &&
+              cudaHostAlloc(&S->h_items, sizeof(unsigned long long) * kRingSize,
+                            cudaHostAllocMapped) == cudaSuccess &&
+              cudaHostAlloc(&S->h_tail, sizeof(unsigned long long), cudaHostAllocMapped) ==
+                  cudaSuccess &&
+              cudaHostAlloc(&S->h_stop, sizeof(unsigned), cudaHostAllocMapped) == cudaSuccess &&
+              cudaHostAlloc(&S->h_complete, sizeof(unsigned) * c.max_requests,
+                            cudaHostAllocMapped) == cudaSuccess &&
+              cudaHostAlloc(&S->h_errs, sizeof(unsigned) * c.max_requests, 0) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&S->s_copy, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&S->s_loop, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&S->ev_loop, cudaEventDisableTiming) == cudaSuccess;
+    if (ok) {
+        *S->h_tail = 0;
+        *S->h_stop = 0;
+        std::memset(S->h_complete, 0, sizeof(unsigned) * c.max_requests);
+        void *p = nullptr;
+        S->dev.desc = S->d_desc;
+        S->dev.done = S->d_done;
+        S->dev.head = S->d_head;
+        ok = cudaHostGetDevicePointer(&p, S->h_items, 0) == cudaSuccess;
+        S->dev.items = static_cast<const unsigned long long *>(p);
+        ok = ok && cudaHostGetDevicePointer(&p, S->h_tail, 0) == cudaSuccess;
+        S->dev.tail = static_cast<const unsigned long long *>(p);
+        ok = ok && cudaHostGetDevicePointer(&p, S->h_stop, 0) == cudaSuccess;
+        S->dev.stop = static_cast<const unsigned *>(p);
+        ok = ok && cudaHostGetDevicePointer(&p, S->h_complete, 0) == cudaSuccess;
+        S->dev.complete = static_cast<unsigned *>(p);
+        S->dev.idle_ns = (unsigned long long)c.idle_exit_us * 1000ull;
+    }
+    if (!ok) {
+        cudaGetLastError();
+        ctx->serve = S;
+        pf_serve_stop(ctx);
+        return ctx->fail(PF_ENOMEM, "serve allocation failed");
+    }
+    S->free_list[0] = budget;
+    S->slot_epoch.assign(c.max_requests, 0);
+    for (int i = c.max_requests - 1; i >= 0; --i) S->free_slots.push_back(i);
+    ctx->serve = S;
+    S->th = std::thread(scheduler, ctx, S);
+    return PF_OK;
+}
+
+pf_status pf_serve_resume(pf_ctx *ctx) {
+    if (!ctx || !ctx->serve) return PF_EBUSY;
+    ctx->serve->paused = false;
+    ctx->serve->cv_work.notify_all();
+    return PF_OK;
+}
+
+pf_status pf_submit(pf_ctx *ctx, const pf_request *req, uint64_t *ticket) {
+    if (!ctx) return PF_EINVAL;
+    ServeState *S = ctx->serve;
+    if (!S) return ctx->fail(PF_EBUSY, "not serving");
+    if (!req || !ticket || req->n < 0 || (req->deciders & 3u) == 0 || (req->deciders & ~3u))
+        return ctx->fail(PF_EINVAL, "malformed request");
+    if (!req->byte_off || (req->n > 0 && (!req->reads || !req->refs || !req->E ||
+                                          !req->accept || !req->count || !req->dist)))
+        return ctx->fail(PF_EINVAL, "malformed request: null pointer");
+    int64_t words = 0;
+    for (int64_t p = 0; p < req->n; ++p) {
+        const int64_t len = req->byte_off[p + 1] - req->byte_off[p];
+        if (len < 0) return ctx->fail(PF_EINVAL, "malformed request: offsets decrease");
+        if (req->E[p] < 0 || req->E[p] > PF_MAX_E)
+            return ctx->fail(PF_EINVAL, "malformed request: E outside [0, %d]", PF_MAX_E);
+        words += (len + 31) / 32;
+    }
+    auto q = std::make_shared<ServeReq>();
+    q->req = *req;
+    q->total_bytes = req->n ? req->byte_off[req->n] - req->byte_off[0] : 0;
+    q->total_words = words;
+    q->nchunks = (int)((req->n + S->cfg.chunk_pairs - 1) / S->cfg.chunk_pairs);
+    q->bytes = request_bytes(*req, q->total_bytes, words);
+    if (q->bytes > S->budget || (uint64_t)q->nchunks > kRingSize)
+        return ctx->fail(PF_ENOMEM, "request needs %zu device bytes, budget %zu", q->bytes,
+                         S->budget);
+    if (cudaEventCreateWithFlags(&q->ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return ctx->fail(PF_ECUDA, "event creation failed");
+    }
+    q->t_submit = std::chrono::steady_clock::now();
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        q->ticket = S->next_ticket++;
+        S->pending.push_back(q);
+        S->reqs[q->ticket] = q;
+        S->stats.submitted++;
+    }
+    S->cv_work.notify_all();
+    *ticket = q->ticket;
+    return PF_OK;
+}
+
+pf_status pf_poll(pf_ctx *ctx, uint64_t ticket, int *done) {
+    if (!ctx || !done) return PF_EINVAL;
+    ServeState *S = ctx->serve;
+    if (!S) return PF_EBUSY;
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return PF_EINVAL;
+    *done = it->second->state == ServeReq::DONE;
+    return PF_OK;
+}
+
+pf_status pf_wait(pf_ctx *ctx, uint64_t ticket, int timeout_ms, double *latency_ms) {
+    if (!ctx) return PF_EINVAL;
+    ServeState *S = ctx->serve;
+    if (!S) return PF_EBUSY;
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return PF_EINVAL;
+    auto q = it->second;
+    auto ready = [&] { return q->state == ServeReq::DONE; };
+    S->waiters++;
+    bool ok = true;
+    if (timeout_ms < 0) S->cv_done.wait(lk, ready);
+    else ok = S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready);
+    S->waiters--;
+    S->cv_idle.notify_all();
+    if (!ok) return PF_ETIMEOUT;
+    if (latency_ms)
+        *latency_ms =
+            std::chrono::duration<double, std::milli>(q->t_done - q->t_submit).count();
+    if (q->ev) cudaEventDestroy(q->ev);
+    q->ev = nullptr;
+    S->reqs.erase(ticket);
+    return q->status;
+}
+
+pf_status pf_serve_stats_get(pf_ctx *ctx, pf_serve_stats *out) {
+    if (!ctx || !out) return PF_EINVAL;
+    ServeState *S = ctx->serve;
+    if (!S) return PF_EBUSY;
+    std::lock_guard<std::mutex> lk(S->mu);
+    *out = S->stats;
+    return PF_OK;
+}
+
+pf_status pf_serve_stop(pf_ctx *ctx) {
+    if (!ctx) return PF_EINVAL;
+    ServeState *S = ctx->serve;
+    if (!S) return PF_EBUSY;
+    cudaSetDevice(ctx->device);
+    if (S->h_stop) *(volatile unsigned *)S->h_stop = 1;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->quit = true;
+    }
+    S->cv_work.notify_all();
+    if (S->th.joinable()) S->th.join();
+    if (S->s_loop) cudaStreamSynchronize(S->s_loop);
+    if (S->s_copy) cudaStreamSynchronize(S->s_copy);
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        for (auto &kv : S->reqs)
+            if (kv.second->state != ServeReq::DONE) finish_req(*S, *kv.second, PF_ECANCELLED);
+        S->pending.clear();
+    }
+    S->cv_done.notify_all();
+    {   // let every thread inside pf_wait leave before S goes away
+        std::unique_lock<std::mutex> lk(S->mu);
+        S->cv_idle.wait(lk, [&] { return S->waiters == 0; });
+    }
+    for (auto &kv : S->reqs)
+        if (kv.second->ev) cudaEventDestroy(kv.second->ev);
+    if (S->arena) cudaFree(S->arena);
+    if (S->d_desc) cudaFree(S->d_desc);
+    if (S->d_done) cudaFree(S->d_done);
+    if (S->d_head) cudaFree(S->d_head);
+    if (S->h_desc) cudaFreeHost(S->h_desc);
+    if (S->h_items) cudaFreeHost(S->h_items);
+    if (S->h_tail) cudaFreeHost(S->h_tail);
+    if (S->h_stop) cudaFreeHost(S->h_stop);
+    if (S->h_complete) cudaFreeHost(S->h_complete);
+    if (S->h_errs) cudaFreeHost(S->h_errs);
+    if (S->s_copy) cudaStreamDestroy(S->s_copy);
+    if (S->s_loop) cudaStreamDestroy(S->s_loop);
+    if (S->ev_loop) cudaEventDestroy(S->ev_loop);
+    ctx->serve = nullptr;
+    delete S;
+    return PF_OK;
+}
+
+}  // extern "C"

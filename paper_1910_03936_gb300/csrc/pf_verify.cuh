@@ -52,11 +52,11 @@ __device__ __forceinline__ U window(uint32_t a, uint32_t b, uint32_t c, unsigned
     }
 }
 
-template <typename U>
+template <typename U, typename L = LdNC>
 __device__ __forceinline__ int verify_pair(const PairsView &pv, int64_t p, int m, int E) {
     if (m == 0) return 0;
     const int W = (m + 31) >> 5;
-    const int64_t rb = pv.read.start(p), fb = pv.ref.start(p);
+    const int64_t rb = pv.read.template start<L>(p), fb = pv.ref.template start<L>(p);
     const int BW = 2 * E + 1;                       // band width (bits used)
     const U band_mask = (BW >= (int)(8 * sizeof(U))) ? ~U(0) : ((U(1) << BW) - 1);
     const U store_mask = (U(1) << (2 * E)) - 1;     // 2E stored differences
@@ -72,10 +72,10 @@ __device__ __forceinline__ int verify_pair(const PairsView &pv, int64_t p, int m
     // read words q0 .. q0+2 where q0 = floor(s / 32).
     int s = -E;                   // s for column j = 1
     int q0 = (s >= 0) ? (s >> 5) : -1;
-    Word3 r0 = load_word(pv.read, rb, q0, W);
-    Word3 r1 = load_word(pv.read, rb, q0 + 1, W);
-    Word3 r2 = load_word(pv.read, rb, q0 + 2, W);
-    Word3 f = load_word(pv.ref, fb, 0, W);
+    Word3 r0 = load_word<L>(pv.read, rb, q0, W);
+    Word3 r1 = load_word<L>(pv.read, rb, q0 + 1, W);
+    Word3 r2 = load_word<L>(pv.read, rb, q0 + 2, W);
+    Word3 f = load_word<L>(pv.ref, fb, 0, W);
 
     for (int j = 1; j <= m; ++j, ++s) {
         const int q = s >> 5;    // arithmetic shift: floor for negatives
@@ -83,7 +83,7 @@ __device__ __forceinline__ int verify_pair(const PairsView &pv, int64_t p, int m
             q0 = q;
             r0 = r1;
             r1 = r2;
-            r2 = load_word(pv.read, rb, q0 + 2, W);
+            r2 = load_word<L>(pv.read, rb, q0 + 2, W);
         }
         const unsigned sh = (unsigned)s & 31u;
         const U wlo = window<U>(r0.lo, r1.lo, r2.lo, sh);
@@ -91,7 +91,7 @@ __device__ __forceinline__ int verify_pair(const PairsView &pv, int64_t p, int m
         const U wnm = window<U>(r0.nm, r1.nm, r2.nm, sh);
         // reference base F[j-1]
         const int fbit = (j - 1) & 31;
-        if (fbit == 0 && j > 1) f = load_word(pv.ref, fb, (j - 1) >> 5, W);
+        if (fbit == 0 && j > 1) f = load_word<L>(pv.ref, fb, (j - 1) >> 5, W);
         const U mlo = U(0) - U((f.lo >> fbit) & 1u);
         const U mhi = U(0) - U((f.hi >> fbit) & 1u);
         const U fn = U(0) - U((f.nm >> fbit) & 1u);
