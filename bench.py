@@ -153,6 +153,49 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# serving: offered-load replay through the device-resident loop
+
+def serve_measure(pf, ctx, seconds_per_load, seed):
+    """Requests of log-uniform size in [1e3, 2e5] pairs, lengths uniform over
+    {100, 150, 250}, E = round(r * len) with r ~ U[0, 0.10), 20/80 mix of
+    pairs within / beyond E (the serving recipe of synth).  Peak = pairs/s of
+    a burst of every request at once; then Poisson arrivals at 25/50/90% of
+    that peak.  Latency = submit to results in host memory."""
+    import torch
+    import synth
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(np.log(1e3), np.log(2e5), size=48)).astype(np.int64)
+    pool, keep, p0 = [], [], 0
+    for n in sizes:
+        P = synth.generate(synth.SERVE, seed, int(n), kmax=60, p0=p0)
+        p0 += int(n)
+        pinned = [torch.from_numpy(a).pin_memory() for a in (P.reads, P.refs)]
+        keep.append(pinned)
+        pool.append(pf.Request(3, pinned[0].numpy(), pinned[1].numpy(), P.read_off, P.E))
+    mean_pairs = float(sizes.mean())
+    pf.pf_serve_start(ctx)
+    pf.pf_serve_replay(ctx, pool[:8], np.zeros(8))           # warm-up
+    burst = np.zeros(4 * len(pool))
+    st, lat, el = pf.pf_serve_replay(ctx, pool, burst)
+    peak = 4 * float(sizes.sum()) / el
+    out = {"peak_pairs_s": peak, "requests_pool": len(pool), "mean_request_pairs": mean_pairs,
+           "status": int(st)}
+    for frac in (0.25, 0.5, 0.9):
+        lam = frac * peak / mean_pairs
+        count = max(50, int(lam * seconds_per_load))
+        arr = np.cumsum(rng.exponential(1.0 / lam, size=count))
+        st, lat, el = pf.pf_serve_replay(ctx, pool, arr)
+        done_pairs = float(sum(sizes[i % len(pool)] for i in range(count)))
+        out["load_%d" % int(frac * 100)] = {
+            "offered_pairs_s": frac * peak, "throughput_pairs_s": done_pairs / el,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "requests": count, "status": int(st)}
+    out["stats"] = pf.pf_serve_stats_get(ctx)
+    pf.pf_serve_stop(ctx)
+    return out
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 
 def main_gpu(args):
@@ -257,6 +300,12 @@ def main_gpu(args):
         ms = float(tt.item())
     pack_ms = statistics.mean(r[0].elapsed_time(r[1]) for r in recs)
     fv_ms = statistics.mean(r[1].elapsed_time(r[3]) for r in recs)
+    if args.stage == "serve":
+        out = serve_measure(pf, ctx, args.serve_seconds, SEED + 5 + rank)
+        if rank == 0:
+            print(json.dumps({"stage": "serve", "serve": out}), flush=True)
+        pf.pf_destroy(ctx)
+        return
     if args.stage != "step":
         dec = args.deciders
         fn = pf.pf_filter_plain if args.stage == "filter_plain" else pf.pf_filter
@@ -333,6 +382,8 @@ def main_gpu(args):
         e2e_ms = float(tt.item())
     pf.pf_sync(ctx)
 
+    serve = None if args.no_serve else serve_measure(pf, ctx, args.serve_seconds, SEED + 5 + rank)
+
     pk, pk_kind = peaks()
     stages = {"pack": pack_ms, "filter": filt_ms, "compact": compact_ms, "verify": verify_ms}
     dominant = max(stages, key=stages.get)
@@ -372,6 +423,7 @@ def main_gpu(args):
                 "h2d_bytes_per_step": 2 * n * M,
                 "d2h_bytes_per_step": n * (2 + 4 + 4)},
         "gpu_launches": None,
+        "serve": serve,
         "clocks": clk,
         "gen_s": t_gen,
     }
@@ -405,9 +457,11 @@ def main():
                     help="time the step only (for profiling): no side measurements")
     ap.add_argument("--cfg", type=int, default=None, help="force batch kernel configuration")
     ap.add_argument("--chunk", type=int, default=64)
-    ap.add_argument("--stage", default="step", choices=["step", "filter_plain", "filter_batched"],
+    ap.add_argument("--stage", default="step", choices=["step", "filter_plain", "filter_batched", "serve"],
                     help="time one filter kernel instead of the step (profiling)")
     ap.add_argument("--deciders", type=int, default=3)
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

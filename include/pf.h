@@ -291,6 +291,9 @@ typedef struct {
 typedef struct {
     uint64_t submitted, completed, failed, pairs_completed;
     uint64_t loop_launches;    /* times the device loop was (re)started */
+    /* seconds summed over completed requests: waiting for admission,
+     * uploading, on the device (published to complete), results back */
+    double queue_s, stage_s, device_s, drain_s;
 } pf_serve_stats;
 
 /* Start serving on ctx (PF_EBUSY if already serving).  Allocates the
@@ -316,6 +319,18 @@ PF_API pf_status pf_wait(pf_ctx *ctx, uint64_t ticket, int timeout_ms, double *l
 PF_API pf_status pf_serve_resume(pf_ctx *ctx);
 
 PF_API pf_status pf_serve_stats_get(pf_ctx *ctx, pf_serve_stats *out);
+
+/* Open-loop load replay, for offered-load measurements: from the calling
+ * thread, submit request pool[i % npool] at arrival_s[i] seconds after the
+ * call (i < count, arrival_s non-decreasing), then wait for all of them.
+ * latency_ms[i] (host, count entries) receives each request's submit-to-
+ * results latency, *elapsed_s the time from the call to the last result.
+ * Requests of the pool may be in flight more than once at a time; their
+ * outputs are then written more than once with the same values.  Returns
+ * the first non-OK request status, PF_OK otherwise. */
+PF_API pf_status pf_serve_replay(pf_ctx *ctx, const pf_request *pool, int npool,
+                                 const double *arrival_s, int count, double *latency_ms,
+                                 double *elapsed_s);
 
 /* Stop the device loop and the scheduler; requests not finished end with
  * PF_ECANCELLED. */

@@ -21,7 +21,7 @@ __all__ = [
     "pf_compact", "pf_verify", "pf_filter_verify", "library_path", "load", "pack_pairs",
     "pf_kernel_configs", "pf_tune_set", "pf_tune_get", "pf_tune", "pf_compact_noalloc",
     "ServeConfig", "Request", "pf_serve_start", "pf_submit", "pf_poll", "pf_wait",
-    "pf_serve_resume", "pf_serve_stats_get", "pf_serve_stop",
+    "pf_serve_resume", "pf_serve_stats_get", "pf_serve_stop", "pf_serve_replay",
 ]
 
 PF_SNEAKYSNAKE = 1
@@ -69,7 +69,9 @@ class _Request(ctypes.Structure):
 class ServeStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
                 ("failed", ctypes.c_uint64), ("pairs_completed", ctypes.c_uint64),
-                ("loop_launches", ctypes.c_uint64)]
+                ("loop_launches", ctypes.c_uint64), ("queue_s", ctypes.c_double),
+                ("stage_s", ctypes.c_double), ("device_s", ctypes.c_double),
+                ("drain_s", ctypes.c_double)]
 
 
 _lib = None
@@ -112,6 +114,7 @@ def load():
         "pf_serve_resume": [P],
         "pf_serve_stats_get": [P, ctypes.POINTER(ServeStats)],
         "pf_serve_stop": [P],
+        "pf_serve_replay": [P, P, I, P, I, P, ctypes.POINTER(ctypes.c_double)],
         "pf_tune_set": [P, U, I, I, I],
         "pf_tune_get": [P, U, I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
         "pf_tune": [P, U, ctypes.POINTER(_Pairs), P, I, I64, I, ctypes.POINTER(ctypes.c_int),
@@ -465,3 +468,17 @@ def pf_serve_stats_get(ctx):
 
 def pf_serve_stop(ctx):
     _check(load().pf_serve_stop(ctx.handle), ctx.handle)
+
+
+def pf_serve_replay(ctx, pool, arrival_s):
+    """Submit pool[i % len(pool)] at arrival_s[i] (seconds from the call)
+    from a C thread, wait for all; returns (status, latency_ms[], elapsed_s)."""
+    import numpy as np
+    arr = (_Request * len(pool))(*[r._c() for r in pool])
+    t = np.ascontiguousarray(arrival_s, dtype=np.float64)
+    lat = np.zeros(max(len(t), 1), dtype=np.float64)
+    el = ctypes.c_double()
+    st = load().pf_serve_replay(ctx.handle, ctypes.cast(arr, ctypes.c_void_p), len(pool),
+                                ctypes.c_void_p(t.ctypes.data), len(t),
+                                ctypes.c_void_p(lat.ctypes.data), ctypes.byref(el))
+    return st, lat[:len(t)], el.value

@@ -37,7 +37,8 @@ constexpr uint64_t kRingSize = 1u << 16;
 // Per-slot request descriptor, in device memory (uploaded with the request).
 struct ServeDesc {
     const uint8_t *reads, *refs;
-    const int64_t *byte_off, *word_off;
+    const int64_t *byte_off;   // the caller's offsets (not rebased)
+    int64_t *word_off;         // filled by the loop, chunk by chunk
     const int16_t *E;
     uint32_t *rlo, *rhi, *rnm, *flo, *fhi, *fnm;
     uint8_t *accept;
@@ -58,6 +59,10 @@ struct ServeDevice {
     const unsigned long long *tail;   // mapped host: items published
     const unsigned *stop;             // mapped host
     unsigned *complete;               // mapped host [max_requests]: epoch of the finished request
+    unsigned long long *last_claim;   // device: globaltimer of the latest claim, any block
+    unsigned long long *dev_tail;     // device: mirror of *tail
+    unsigned long long *last_poll;    // device: globaltimer of the latest mirror refresh
+    unsigned *dev_exit;               // device: set by a block that finds the loop idle or stopped
     unsigned long long idle_ns;
 };
 
@@ -78,6 +83,14 @@ __device__ __forceinline__ unsigned long long ld_relaxed_sys64(const unsigned lo
 }
 __device__ __forceinline__ void st_release_sys(unsigned *p, unsigned v) {
     asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
     unsigned long long t;
@@ -135,32 +148,73 @@ __device__ __forceinline__ void serve_filter_chunk(const ServeDesc &d, const Pai
     }
 }
 
+// Before each launch: the idle clock starts now, the exit flag is clear.
+__global__ void serve_stamp_kernel(unsigned long long *last_claim, unsigned *dev_exit,
+                                   unsigned long long *last_poll) {
+    *last_claim = globaltimer_ns();
+    *dev_exit = 0u;
+    *last_poll = 0ull;
+}
+
+// Claiming work.  No block ever waits for another one: every block may
+// refresh the device-side mirror of the ring tail from host memory (at most
+// one refresh per 2 microseconds across the grid, arbitrated by a
+// compare-and-swap on the time of the last refresh), and every block
+// decides on its own that the loop is idle: no claim by any block for
+// idle_ns and nothing published beyond the head in host memory.  A block
+// that finds the loop idle or stopped raises dev_exit so the others leave
+// at their next poll.  Returns 1 with *item set, or 0 to leave.
+__device__ int serve_claim(const ServeDevice &sd, unsigned long long *item) {
+    unsigned nap = 500;
+    for (unsigned polls = 0; polls < (1u << 22); ++polls) {
+        const unsigned long long t = ld_acquire_gpu(sd.dev_tail);
+        const unsigned long long h = *(volatile unsigned long long *)sd.head;
+        if (h < t) {
+            if (atomicCAS(sd.head, h, h + 1) == h) {
+                *item = ld_relaxed_sys64(sd.items + (h % kRingSize));
+                atomicMax(sd.last_claim, globaltimer_ns());
+                return 1;
+            }
+            continue;  // another block took it: look again at once
+        }
+        if (*(volatile unsigned *)sd.dev_exit) return 0;
+        const unsigned long long now = globaltimer_ns();
+        const unsigned long long lp = *(volatile unsigned long long *)sd.last_poll;
+        const unsigned long long last = *(volatile unsigned long long *)sd.last_claim;
+        const bool idle = now > last && now - last > sd.idle_ns;
+        if (idle || (now > lp + 2000 && atomicCAS(sd.last_poll, lp, now) == lp)) {
+            if (ld_relaxed_sys(sd.stop)) {
+                atomicExch(sd.dev_exit, 1u);
+                return 0;
+            }
+            const unsigned long long ht = ld_acquire_sys(sd.tail);
+            if (ht > t) {
+                __threadfence();  // the items the host wrote before ht, then the mirror
+                atomicMax(sd.dev_tail, ht);
+                nap = 500;
+                continue;
+            }
+            if (idle) {
+                atomicExch(sd.dev_exit, 1u);
+                return 0;
+            }
+        }
+        __nanosleep(nap);
+        nap = nap < 16000 ? nap * 2 : 16000;
+    }
+    return 0;
+}
+
 __global__ void __launch_bounds__(kServeThreads) serve_loop_kernel(ServeDevice sd) {
     __shared__ unsigned long long s_item;
     __shared__ int s_cmd;
     __shared__ int64_t s_woff[kServeMaxChunk + 1];
     __shared__ int64_t s_boff[kServeMaxChunk + 1];
-    unsigned long long last_work = globaltimer_ns();
     for (;;) {
         if (threadIdx.x == 0) {
-            int cmd = 0;
-            for (unsigned polls = 0;; ++polls) {
-                if (ld_relaxed_sys(sd.stop)) break;
-                const unsigned long long t = ld_acquire_sys(sd.tail);
-                const unsigned long long h = *(volatile unsigned long long *)sd.head;
-                if (h < t) {
-                    if (atomicCAS(sd.head, h, h + 1) == h) {
-                        s_item = ld_relaxed_sys64(sd.items + (h % kRingSize));
-                        cmd = 1;
-                        break;
-                    }
-                    continue;  // another block took it: look again at once
-                }
-                const unsigned long long now = globaltimer_ns();
-                if (now - last_work > sd.idle_ns || polls > (1u << 26)) break;
-                __nanosleep(2000);
-            }
-            s_cmd = cmd;
+            unsigned long long it = 0;
+            s_cmd = serve_claim(sd, &it);
+            s_item = it;
         }
         __syncthreads();
         if (s_cmd == 0) return;
@@ -172,10 +226,16 @@ __global__ void __launch_bounds__(kServeThreads) serve_loop_kernel(ServeDevice s
         const int64_t c1 = min(d.n, c0 + (int64_t)d.chunk);
         const int np = (int)(c1 - c0);
 
-        // ---- pack the chunk's reads and references (a1)
+        // ---- pack the chunk's reads and references (a1).  Sequence s of the
+        // request starts at word floor(b_s / 32) + s, b_s its byte offset from
+        // the request's first byte: never overlapping (floor((b+L)/32) + 1 >=
+        // floor(b/32) + ceil(L/32)), computable per chunk without a scan.
+        const int64_t b00 = __ldcg(d.byte_off);
         for (int i = threadIdx.x; i <= np; i += blockDim.x) {
-            s_woff[i] = __ldcg(d.word_off + c0 + i);
-            s_boff[i] = __ldcg(d.byte_off + c0 + i);
+            const int64_t b = __ldcg(d.byte_off + c0 + i) - b00;
+            s_boff[i] = b;
+            s_woff[i] = (b >> 5) + c0 + i;
+            if (i < np) d.word_off[c0 + i] = s_woff[i];
         }
         __syncthreads();
         const int64_t wbase = s_woff[0];
@@ -189,6 +249,7 @@ __global__ void __launch_bounds__(kServeThreads) serve_loop_kernel(ServeDevice s
             }
             const int w = (int)(gw - s_woff[l]);
             const int len = (int)(s_boff[l + 1] - s_boff[l]);
+            if (w >= (len + 31) / 32) continue;  // gap word between sequences
             pack_word<LdCG>(d.reads + s_boff[l], len, w, d.rlo + gw, d.rhi + gw, d.rnm + gw, d.err);
             pack_word<LdCG>(d.refs + s_boff[l], len, w, d.flo + gw, d.fhi + gw, d.fnm + gw, d.err);
         }
@@ -207,7 +268,7 @@ __global__ void __launch_bounds__(kServeThreads) serve_loop_kernel(ServeDevice s
         // decider's flags are slot 0
         for (int64_t p = c0 + threadIdx.x; p < c1; p += blockDim.x) {
             const int E = __ldcg(d.E + p);
-            const int m = (int)(s_boff[p - c0 + 1] - s_boff[p - c0]);
+            const int m = (int)(s_boff[p - c0 + 1] - s_boff[p - c0]);  // byte offsets
             int32_t v;
             if (m < 0 || E < 0 || E > PF_MAX_E) v = -1;
             else if (__ldcg(d.accept + p)) v = verify_pair<uint64_t, LdCG>(pv, p, m, E);
@@ -223,7 +284,6 @@ __global__ void __launch_bounds__(kServeThreads) serve_loop_kernel(ServeDevice s
                 st_release_sys(sd.complete + slot, d.epoch);
             }
         }
-        last_work = globaltimer_ns();
     }
 }
 
@@ -234,50 +294,33 @@ struct ServeReq {
     uint64_t ticket = 0;
     pf_request req{};
     int slot = -1;
-    size_t off = 0, bytes = 0;
+    size_t off = 0, bytes = 0;     // device arena
+    size_t hoff = 0, hbytes = 0;   // pinned staging arena
     int64_t total_bytes = 0, total_words = 0;
     int nchunks = 0;
     unsigned epoch = 0;
+    bool pinned_in = false;        // reads and refs are page-locked
     enum State { PENDING, STAGING, RUNNING, DRAINING, DONE } state = PENDING;
     cudaEvent_t ev = nullptr;
-    std::chrono::steady_clock::time_point t_submit, t_done;
+    using tp = std::chrono::steady_clock::time_point;
+    tp t_submit, t_admit, t_pub, t_seen, t_done;
     pf_status status = PF_OK;
-    unsigned *h_err = nullptr;  // pinned, per slot
+    // pinned staging pieces
+    int64_t *h_boff = nullptr;
+    int16_t *h_E = nullptr;
+    uint8_t *h_acc = nullptr;
+    int16_t *h_cnt = nullptr;
+    int32_t *h_dist = nullptr;
+    unsigned *h_err = nullptr;
 };
 
-struct ServeState {
-    pf_serve_config cfg{};
-    int device = 0;
-    size_t budget = 0;
-    char *arena = nullptr;
+// First-fit allocator over [0, size) for the two arenas.
+struct Arena {
     std::map<size_t, size_t> free_list;  // offset -> size
-    ServeDesc *d_desc = nullptr;
-    ServeDesc *h_desc = nullptr;         // pinned staging, one per slot
-    unsigned *d_done = nullptr;
-    unsigned long long *d_head = nullptr;
-    unsigned long long *h_items = nullptr, *h_tail = nullptr;
-    unsigned *h_stop = nullptr, *h_complete = nullptr, *h_errs = nullptr;
-    ServeDevice dev{};
-    cudaStream_t s_copy = nullptr, s_loop = nullptr;
-    cudaEvent_t ev_loop = nullptr;
-    bool loop_running = false;
-    std::atomic<bool> paused{false};
-    uint64_t published = 0;   // items published (host copy of *h_tail)
-    uint64_t inflight_items = 0;
-
-    std::mutex mu;
-    std::condition_variable cv_work, cv_done, cv_idle;
-    bool quit = false;
-    int waiters = 0;      // threads inside pf_wait
-    std::thread th;
-    uint64_t next_ticket = 1;
-    std::deque<std::shared_ptr<ServeReq>> pending;
-    std::map<uint64_t, std::shared_ptr<ServeReq>> reqs;
-    std::vector<int> free_slots;
-    std::vector<unsigned> slot_epoch;
-    pf_serve_stats stats{};
-    std::string fatal;
-
+    void reset(size_t size) {
+        free_list.clear();
+        if (size) free_list[0] = size;
+    }
     bool alloc(size_t bytes, size_t *off) {
         for (auto it = free_list.begin(); it != free_list.end(); ++it) {
             if (it->second >= bytes) {
@@ -308,21 +351,79 @@ struct ServeState {
     }
 };
 
+struct ServeState {
+    pf_serve_config cfg{};
+    int device = 0;
+    size_t budget = 0, stage_budget = 0;
+    char *arena = nullptr;         // device
+    char *stage_mem = nullptr;     // pinned host
+    Arena dev_arena, host_arena;
+    ServeDesc *d_desc = nullptr;
+    ServeDesc *h_desc = nullptr;   // pinned staging, one per slot
+    unsigned *d_done = nullptr;
+    unsigned long long *d_head = nullptr, *d_last = nullptr, *d_tail = nullptr, *d_poll = nullptr;
+    unsigned *d_exit = nullptr;
+    unsigned long long *h_items = nullptr, *h_tail = nullptr;
+    unsigned *h_stop = nullptr, *h_complete = nullptr;
+    ServeDevice dev{};
+    cudaStream_t s_copy = nullptr, s_loop = nullptr;
+    cudaEvent_t ev_loop = nullptr;
+    bool loop_running = false;
+    std::atomic<bool> paused{false};
+    uint64_t published = 0;        // items published (host copy of *h_tail)
+    uint64_t inflight_items = 0;
+
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done, cv_idle;
+    bool quit = false;
+    int waiters = 0;               // threads inside pf_wait
+    std::thread th;
+    uint64_t next_ticket = 1;
+    std::deque<std::shared_ptr<ServeReq>> pending;
+    std::vector<std::shared_ptr<ServeReq>> active;      // admitted, not done
+    std::map<uint64_t, std::shared_ptr<ServeReq>> reqs; // every unreleased ticket
+    std::vector<int> free_slots;
+    std::vector<unsigned> slot_epoch;
+    pf_serve_stats stats{};
+    std::string fatal;
+};
+
 namespace {
 
 inline size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
+inline int slots_of(unsigned deciders) { return deciders == 3u ? 2 : 1; }
 
 // Device bytes a request needs in the arena.
 size_t request_bytes(const pf_request &r, int64_t total_bytes, int64_t total_words) {
-    const int slots = (r.deciders == 3u) ? 2 : 1;
-    const size_t n = (size_t)r.n;
+    const size_t n = (size_t)r.n, sl = (size_t)slots_of(r.deciders);
     return up256((size_t)total_bytes) * 2 + up256((n + 1) * 8) * 2 + up256(n * 2) +
-           up256((size_t)total_words * 4) * 6 + up256(slots * n) + up256(slots * n * 2) +
+           up256((size_t)total_words * 4) * 6 + up256(sl * n) + up256(sl * n * 2) +
            up256(n * 4) + 256;
 }
 
-void stage(pf_ctx *ctx, ServeState &S, ServeReq &q) {
+// Pinned staging bytes: offsets and thresholds in, results out.
+size_t staging_bytes(const pf_request &r) {
+    const size_t n = (size_t)r.n, sl = (size_t)slots_of(r.deciders);
+    return up256((n + 1) * 8) + up256(n * 2) + up256(sl * n) + up256(sl * n * 2) +
+           up256(n * 4) + 256;
+}
+
+bool is_pinned(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+double secs(ServeReq::tp a, ServeReq::tp b) {
+    return std::chrono::duration<double>(b - a).count();
+}
+
+void stage(ServeState &S, ServeReq &q) {
     const pf_request &r = q.req;
+    const size_t n = (size_t)r.n, sl = (size_t)slots_of(r.deciders);
     char *b = S.arena + q.off;
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -330,22 +431,19 @@ void stage(pf_ctx *ctx, ServeState &S, ServeReq &q) {
         o += up256(bytes);
         return p;
     };
-    const int slots = (r.deciders == 3u) ? 2 : 1;
-    const size_t n = (size_t)r.n;
     ServeDesc &d = S.h_desc[q.slot];
     d.reads = reinterpret_cast<uint8_t *>(take((size_t)q.total_bytes));
     d.refs = reinterpret_cast<uint8_t *>(take((size_t)q.total_bytes));
     int64_t *boff = reinterpret_cast<int64_t *>(take((n + 1) * 8));
-    int64_t *woff = reinterpret_cast<int64_t *>(take((n + 1) * 8));
     d.byte_off = boff;
-    d.word_off = woff;
+    d.word_off = reinterpret_cast<int64_t *>(take((n + 1) * 8));
     d.E = reinterpret_cast<int16_t *>(take(n * 2));
     uint32_t *pl[6];
     for (auto &x : pl) x = reinterpret_cast<uint32_t *>(take((size_t)q.total_words * 4));
     d.rlo = pl[0]; d.rhi = pl[1]; d.rnm = pl[2];
     d.flo = pl[3]; d.fhi = pl[4]; d.fnm = pl[5];
-    d.accept = reinterpret_cast<uint8_t *>(take(slots * n));
-    d.count = reinterpret_cast<int16_t *>(take(slots * n * 2));
+    d.accept = reinterpret_cast<uint8_t *>(take(sl * n));
+    d.count = reinterpret_cast<int16_t *>(take(sl * n * 2));
     d.dist = reinterpret_cast<int32_t *>(take(n * 4));
     d.err = reinterpret_cast<unsigned *>(take(4));
     d.n = r.n;
@@ -354,88 +452,137 @@ void stage(pf_ctx *ctx, ServeState &S, ServeReq &q) {
     d.deciders = r.deciders;
     d.epoch = q.epoch;
 
-    // host-side offsets: rebased bytes and word starts
-    std::vector<int64_t> hb(n + 1), hw(n + 1);
-    int64_t acc = 0;
-    for (size_t p = 0; p <= n; ++p) {
-        hb[p] = r.byte_off[p] - r.byte_off[0];
-        hw[p] = acc;
-        if (p < n) acc += (r.byte_off[p + 1] - r.byte_off[p] + 31) / 32;
-    }
+    // pinned staging pieces
+    char *h = S.stage_mem + q.hoff;
+    size_t ho = 0;
+    auto htake = [&](size_t bytes) {
+        char *p = h + ho;
+        ho += up256(bytes);
+        return p;
+    };
+    q.h_boff = reinterpret_cast<int64_t *>(htake((n + 1) * 8));
+    q.h_E = reinterpret_cast<int16_t *>(htake(n * 2));
+    q.h_acc = reinterpret_cast<uint8_t *>(htake(sl * n));
+    q.h_cnt = reinterpret_cast<int16_t *>(htake(sl * n * 2));
+    q.h_dist = reinterpret_cast<int32_t *>(htake(n * 4));
+    q.h_err = reinterpret_cast<unsigned *>(htake(4));
+    std::memcpy(q.h_boff, r.byte_off, (n + 1) * 8);
+    if (n) std::memcpy(q.h_E, r.E, n * 2);
+
     cudaStream_t st = S.s_copy;
-    const uint8_t *src_r = r.reads + r.byte_off[0];
-    const uint8_t *src_f = r.refs + r.byte_off[0];
     if (q.total_bytes) {
-        cudaMemcpyAsync((void *)d.reads, src_r, (size_t)q.total_bytes, cudaMemcpyHostToDevice, st);
-        cudaMemcpyAsync((void *)d.refs, src_f, (size_t)q.total_bytes, cudaMemcpyHostToDevice, st);
+        // page-locked inputs go straight to the copy engine; pageable ones are
+        // staged by the driver (the call returns once they are read)
+        cudaMemcpyAsync((void *)d.reads, r.reads + r.byte_off[0], (size_t)q.total_bytes,
+                        cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync((void *)d.refs, r.refs + r.byte_off[0], (size_t)q.total_bytes,
+                        cudaMemcpyHostToDevice, st);
     }
-    cudaMemcpyAsync(boff, hb.data(), (n + 1) * 8, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(woff, hw.data(), (n + 1) * 8, cudaMemcpyHostToDevice, st);
-    if (n) cudaMemcpyAsync((void *)d.E, r.E, n * 2, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(boff, q.h_boff, (n + 1) * 8, cudaMemcpyHostToDevice, st);
+    if (n) cudaMemcpyAsync((void *)d.E, q.h_E, n * 2, cudaMemcpyHostToDevice, st);
     cudaMemsetAsync(d.err, 0, 4, st);
     cudaMemsetAsync(S.d_done + q.slot, 0, sizeof(unsigned), st);
     cudaMemcpyAsync(S.d_desc + q.slot, &d, sizeof(ServeDesc), cudaMemcpyHostToDevice, st);
     cudaEventRecord(q.ev, st);
-    (void)ctx;
 }
 
 void drain(ServeState &S, ServeReq &q) {
     const pf_request &r = q.req;
     const ServeDesc &d = S.h_desc[q.slot];
-    const int slots = (r.deciders == 3u) ? 2 : 1;
-    const size_t n = (size_t)r.n;
+    const size_t n = (size_t)r.n, sl = (size_t)slots_of(r.deciders);
     cudaStream_t st = S.s_copy;
     if (n) {
-        cudaMemcpyAsync(r.accept, d.accept, slots * n, cudaMemcpyDeviceToHost, st);
-        cudaMemcpyAsync(r.count, d.count, slots * n * 2, cudaMemcpyDeviceToHost, st);
-        cudaMemcpyAsync(r.dist, d.dist, n * 4, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(q.h_acc, d.accept, sl * n, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(q.h_cnt, d.count, sl * n * 2, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(q.h_dist, d.dist, n * 4, cudaMemcpyDeviceToHost, st);
     }
-    cudaMemcpyAsync(S.h_errs + q.slot, d.err, 4, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(q.h_err, d.err, 4, cudaMemcpyDeviceToHost, st);
     cudaEventRecord(q.ev, st);
 }
 
-void finish_req(ServeState &S, ServeReq &q, pf_status st) {
+// Results to the caller's buffers, resources back to the pools (scheduler
+// thread, or pf_serve_stop after the thread has ended).
+void finish_req(ServeState &S, ServeReq &q, pf_status st, bool copy_out) {
+    const pf_request &r = q.req;
+    const size_t n = (size_t)r.n, sl = (size_t)slots_of(r.deciders);
+    if (copy_out && n) {
+        std::memcpy(r.accept, q.h_acc, sl * n);
+        std::memcpy(r.count, q.h_cnt, sl * n * 2);
+        std::memcpy(r.dist, q.h_dist, n * 4);
+    }
     q.status = st;
-    q.state = ServeReq::DONE;
     q.t_done = std::chrono::steady_clock::now();
     if (q.slot >= 0) {
         S.free_slots.push_back(q.slot);
-        S.release(q.off, q.bytes);
+        S.dev_arena.release(q.off, q.bytes);
+        S.host_arena.release(q.hoff, q.hbytes);
         S.inflight_items -= (uint64_t)q.nchunks;
         q.slot = -1;
     }
-    if (st == PF_OK) {
-        S.stats.completed++;
-        S.stats.pairs_completed += (uint64_t)q.req.n;
-    } else {
-        S.stats.failed++;
-    }
 }
 
-void scheduler(pf_ctx *ctx, ServeState *Sp) {
+// The scheduler thread owns the admission queue, the active list, the
+// arenas, the slots and the ring; the mutex guards only the hand-offs with
+// callers (new submissions in, finished requests out), so submitting and
+// waiting never stall behind copies or polling.
+void scheduler(ServeState *Sp) {
     ServeState &S = *Sp;
     cudaSetDevice(S.device);
-    std::unique_lock<std::mutex> lk(S.mu);
-    while (!S.quit) {
+    std::deque<std::shared_ptr<ServeReq>> queue;      // admission order
+    std::vector<std::shared_ptr<ServeReq>> finished;  // to hand back under the lock
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lk(S.mu);
+            for (auto &q : finished) {
+                q->state = ServeReq::DONE;
+                if (q->status == PF_OK) {
+                    S.stats.completed++;
+                    S.stats.pairs_completed += (uint64_t)q->req.n;
+                    S.stats.queue_s += secs(q->t_submit, q->t_admit);
+                    S.stats.stage_s += secs(q->t_admit, q->t_pub);
+                    S.stats.device_s += secs(q->t_pub, q->t_seen);
+                    S.stats.drain_s += secs(q->t_seen, q->t_done);
+                } else {
+                    S.stats.failed++;
+                }
+            }
+            if (!finished.empty()) S.cv_done.notify_all();
+            finished.clear();
+            if (S.quit) break;
+            if (queue.empty() && S.active.empty() && S.pending.empty())
+                S.cv_work.wait_for(lk, std::chrono::milliseconds(20));
+            while (!S.pending.empty()) {
+                queue.push_back(S.pending.front());
+                S.pending.pop_front();
+            }
+        }
         bool progress = false;
-        // admission: FIFO, as slots, device memory and ring room allow
-        while (!S.pending.empty() && !S.free_slots.empty()) {
-            auto q = S.pending.front();
+        // admission: FIFO, as slots, device memory, staging memory and ring room allow
+        while (!queue.empty() && !S.free_slots.empty()) {
+            auto q = queue.front();
             if (S.inflight_items + (uint64_t)q->nchunks > kRingSize) break;
-            size_t off = 0;
-            if (!S.alloc(q->bytes, &off)) break;
-            S.pending.pop_front();
+            size_t off = 0, hoff = 0;
+            if (!S.dev_arena.alloc(q->bytes, &off)) break;
+            if (!S.host_arena.alloc(q->hbytes, &hoff)) {
+                S.dev_arena.release(off, q->bytes);
+                break;
+            }
+            queue.pop_front();
             q->off = off;
+            q->hoff = hoff;
             q->slot = S.free_slots.back();
             S.free_slots.pop_back();
             q->epoch = ++S.slot_epoch[q->slot];
             S.inflight_items += (uint64_t)q->nchunks;
             q->state = ServeReq::STAGING;
-            stage(ctx, S, *q);
+            q->t_admit = std::chrono::steady_clock::now();
+            stage(S, *q);
+            S.active.push_back(q);
             progress = true;
         }
-        for (auto &kv : S.reqs) {
-            ServeReq &q = *kv.second;
+        bool running = false;
+        for (size_t i = 0; i < S.active.size();) {
+            ServeReq &q = *S.active[i];
             if (q.state == ServeReq::STAGING && cudaEventQuery(q.ev) == cudaSuccess) {
                 // publish the request's items, then the new tail
                 for (int c = 0; c < q.nchunks; ++c)
@@ -445,7 +592,9 @@ void scheduler(pf_ctx *ctx, ServeState *Sp) {
                 std::atomic_thread_fence(std::memory_order_release);
                 *(volatile unsigned long long *)S.h_tail = S.published;
                 q.state = ServeReq::RUNNING;
+                q.t_pub = std::chrono::steady_clock::now();
                 if (q.nchunks == 0) {
+                    q.t_seen = q.t_pub;
                     q.state = ServeReq::DRAINING;
                     drain(S, q);
                 }
@@ -453,22 +602,29 @@ void scheduler(pf_ctx *ctx, ServeState *Sp) {
             } else if (q.state == ServeReq::RUNNING &&
                        *(volatile unsigned *)(S.h_complete + q.slot) == q.epoch) {
                 std::atomic_thread_fence(std::memory_order_acquire);
+                q.t_seen = std::chrono::steady_clock::now();
                 q.state = ServeReq::DRAINING;
                 drain(S, q);
                 progress = true;
             } else if (q.state == ServeReq::DRAINING && cudaEventQuery(q.ev) == cudaSuccess) {
-                const unsigned e = S.h_errs[q.slot];
-                finish_req(S, q, (e & ERR_PAIR_ARGS) ? PF_EINVAL : (e & ERR_BYTES) ? PF_EDATA : PF_OK);
-                S.cv_done.notify_all();
+                const unsigned e = *q.h_err;
+                finish_req(S, q,
+                           (e & ERR_PAIR_ARGS) ? PF_EINVAL : (e & ERR_BYTES) ? PF_EDATA : PF_OK,
+                           true);
+                finished.push_back(S.active[i]);
+                S.active[i] = S.active.back();
+                S.active.pop_back();
                 progress = true;
+                continue;
             }
+            running |= q.state == ServeReq::RUNNING;
+            ++i;
         }
         // the device loop: (re)start it while published items wait
         if (S.loop_running && cudaEventQuery(S.ev_loop) == cudaSuccess) S.loop_running = false;
-        bool waiting = false;
-        for (auto &kv : S.reqs)
-            if (kv.second->state == ServeReq::RUNNING) waiting = true;
-        if (waiting && !S.loop_running && !S.paused.load()) {
+        if (running && !S.loop_running && !S.paused.load()) {
+            // the idle clock starts at the launch
+            serve_stamp_kernel<<<1, 1, 0, S.s_loop>>>(S.d_last, S.d_exit, S.d_poll);
             serve_loop_kernel<<<S.cfg.workers, kServeThreads, 0, S.s_loop>>>(S.dev);
             if (cudaGetLastError() != cudaSuccess) {
                 S.fatal = "serve loop launch failed";
@@ -478,18 +634,13 @@ void scheduler(pf_ctx *ctx, ServeState *Sp) {
                 S.stats.loop_launches++;
             }
         }
-        bool busy = !S.pending.empty();
-        for (auto &kv : S.reqs)
-            if (kv.second->state != ServeReq::DONE) busy = true;
-        if (!progress) {
-            if (busy) {
-                lk.unlock();
-                std::this_thread::sleep_for(std::chrono::microseconds(20));
-                lk.lock();
-            } else {
-                S.cv_work.wait_for(lk, std::chrono::milliseconds(20));
-            }
-        }
+        if (!progress && finished.empty() && (!queue.empty() || !S.active.empty()))
+            std::this_thread::sleep_for(std::chrono::microseconds(5));
+    }
+    // requests the thread still owns end cancelled; pf_serve_stop reports them
+    for (auto &q : queue) {
+        std::lock_guard<std::mutex> lk(S.mu);
+        S.pending.push_front(q);
     }
 }
 
@@ -534,11 +685,18 @@ pf_status pf_serve_start(pf_ctx *ctx, const pf_serve_config *cfg) {
     S->cfg = c;
     S->device = ctx->device;
     S->budget = budget;
+    // pinned staging: ~20 B per pair against ~370 B per pair on the device
+    S->stage_budget = std::max<size_t>(budget / 16, size_t(64) << 20) & ~size_t(255);
     S->paused = c.start_paused != 0;
     bool ok = cudaMalloc(&S->arena, budget) == cudaSuccess &&
               cudaMalloc(&S->d_desc, sizeof(ServeDesc) * c.max_requests) == cudaSuccess &&
               cudaMalloc(&S->d_done, sizeof(unsigned) * c.max_requests) == cudaSuccess &&
               cudaMalloc(&S->d_head, sizeof(unsigned long long)) == cudaSuccess &&
+              cudaMalloc(&S->d_last, sizeof(unsigned long long)) == cudaSuccess &&
+              cudaMalloc(&S->d_tail, sizeof(unsigned long long)) == cudaSuccess &&
+              cudaMemset(S->d_tail, 0, sizeof(unsigned long long)) == cudaSuccess &&
+              cudaMalloc(&S->d_exit, sizeof(unsigned)) == cudaSuccess &&
+              cudaMalloc(&S->d_poll, sizeof(unsigned long long)) == cudaSuccess &&
               cudaMemset(S->d_head, 0, sizeof(unsigned long long)) == cudaSuccess &&
               cudaHostAlloc(&S->h_desc, sizeof(ServeDesc) * c.max_requests, 0) == cudaSuccess &&
               cudaHostAlloc(&S->h_items, sizeof(unsigned long long) * kRingSize,
@@ -548,7 +706,7 @@ pf_status pf_serve_start(pf_ctx *ctx, const pf_serve_config *cfg) {
               cudaHostAlloc(&S->h_stop, sizeof(unsigned), cudaHostAllocMapped) == cudaSuccess &&
               cudaHostAlloc(&S->h_complete, sizeof(unsigned) * c.max_requests,
                             cudaHostAllocMapped) == cudaSuccess &&
-              cudaHostAlloc(&S->h_errs, sizeof(unsigned) * c.max_requests, 0) == cudaSuccess &&
+              cudaHostAlloc(&S->stage_mem, S->stage_budget, 0) == cudaSuccess &&
               cudaStreamCreateWithFlags(&S->s_copy, cudaStreamNonBlocking) == cudaSuccess &&
               cudaStreamCreateWithFlags(&S->s_loop, cudaStreamNonBlocking) == cudaSuccess &&
               cudaEventCreateWithFlags(&S->ev_loop, cudaEventDisableTiming) == cudaSuccess;
@@ -560,6 +718,10 @@ pf_status pf_serve_start(pf_ctx *ctx, const pf_serve_config *cfg) {
         S->dev.desc = S->d_desc;
         S->dev.done = S->d_done;
         S->dev.head = S->d_head;
+        S->dev.last_claim = S->d_last;
+        S->dev.dev_tail = S->d_tail;
+        S->dev.dev_exit = S->d_exit;
+        S->dev.last_poll = S->d_poll;
         ok = cudaHostGetDevicePointer(&p, S->h_items, 0) == cudaSuccess;
         S->dev.items = static_cast<const unsigned long long *>(p);
         ok = ok && cudaHostGetDevicePointer(&p, S->h_tail, 0) == cudaSuccess;
@@ -576,11 +738,12 @@ pf_status pf_serve_start(pf_ctx *ctx, const pf_serve_config *cfg) {
         pf_serve_stop(ctx);
         return ctx->fail(PF_ENOMEM, "serve allocation failed");
     }
-    S->free_list[0] = budget;
+    S->dev_arena.reset(budget);
+    S->host_arena.reset(S->stage_budget);
     S->slot_epoch.assign(c.max_requests, 0);
     for (int i = c.max_requests - 1; i >= 0; --i) S->free_slots.push_back(i);
     ctx->serve = S;
-    S->th = std::thread(scheduler, ctx, S);
+    S->th = std::thread(scheduler, S);
     return PF_OK;
 }
 
@@ -600,21 +763,23 @@ pf_status pf_submit(pf_ctx *ctx, const pf_request *req, uint64_t *ticket) {
     if (!req->byte_off || (req->n > 0 && (!req->reads || !req->refs || !req->E ||
                                           !req->accept || !req->count || !req->dist)))
         return ctx->fail(PF_EINVAL, "malformed request: null pointer");
-    int64_t words = 0;
+    bool bad_off = false, bad_E = false;
     for (int64_t p = 0; p < req->n; ++p) {
-        const int64_t len = req->byte_off[p + 1] - req->byte_off[p];
-        if (len < 0) return ctx->fail(PF_EINVAL, "malformed request: offsets decrease");
-        if (req->E[p] < 0 || req->E[p] > PF_MAX_E)
-            return ctx->fail(PF_EINVAL, "malformed request: E outside [0, %d]", PF_MAX_E);
-        words += (len + 31) / 32;
+        bad_off |= req->byte_off[p + 1] < req->byte_off[p];
+        bad_E |= (req->E[p] < 0) | (req->E[p] > PF_MAX_E);
     }
+    if (bad_off) return ctx->fail(PF_EINVAL, "malformed request: offsets decrease");
+    if (bad_E) return ctx->fail(PF_EINVAL, "malformed request: E outside [0, %d]", PF_MAX_E);
+    const int64_t tb = req->n ? req->byte_off[req->n] - req->byte_off[0] : 0;
+    const int64_t words = (tb >> 5) + req->n + 1;
     auto q = std::make_shared<ServeReq>();
     q->req = *req;
     q->total_bytes = req->n ? req->byte_off[req->n] - req->byte_off[0] : 0;
     q->total_words = words;
     q->nchunks = (int)((req->n + S->cfg.chunk_pairs - 1) / S->cfg.chunk_pairs);
     q->bytes = request_bytes(*req, q->total_bytes, words);
-    if (q->bytes > S->budget || (uint64_t)q->nchunks > kRingSize)
+    q->hbytes = staging_bytes(*req);
+    if (q->bytes > S->budget || q->hbytes > S->stage_budget || (uint64_t)q->nchunks > kRingSize)
         return ctx->fail(PF_ENOMEM, "request needs %zu device bytes, budget %zu", q->bytes,
                          S->budget);
     if (cudaEventCreateWithFlags(&q->ev, cudaEventDisableTiming) != cudaSuccess) {
@@ -679,6 +844,42 @@ pf_status pf_serve_stats_get(pf_ctx *ctx, pf_serve_stats *out) {
     return PF_OK;
 }
 
+pf_status pf_serve_replay(pf_ctx *ctx, const pf_request *pool, int npool,
+                          const double *arrival_s, int count, double *latency_ms,
+                          double *elapsed_s) {
+    if (!ctx) return PF_EINVAL;
+    if (!ctx->serve) return ctx->fail(PF_EBUSY, "not serving");
+    if (!pool || npool <= 0 || !arrival_s || count < 0 || (count > 0 && !latency_ms))
+        return ctx->fail(PF_EINVAL, "pf_serve_replay: bad arguments");
+    for (int i = 1; i < count; ++i)
+        if (arrival_s[i] < arrival_s[i - 1])
+            return ctx->fail(PF_EINVAL, "pf_serve_replay: arrival times decrease");
+    using clk = std::chrono::steady_clock;
+    std::vector<uint64_t> tickets((size_t)count, 0);
+    const auto t0 = clk::now();
+    pf_status first = PF_OK;
+    for (int i = 0; i < count; ++i) {
+        const auto due = t0 + std::chrono::duration_cast<clk::duration>(
+                                  std::chrono::duration<double>(arrival_s[i]));
+        while (clk::now() + std::chrono::microseconds(200) < due)
+            std::this_thread::sleep_for(std::chrono::microseconds(100));
+        while (clk::now() < due) std::this_thread::yield();
+        const pf_status st = pf_submit(ctx, &pool[i % npool], &tickets[(size_t)i]);
+        if (st != PF_OK) {
+            if (first == PF_OK) first = st;
+            tickets[(size_t)i] = 0;
+        }
+    }
+    for (int i = 0; i < count; ++i) {
+        latency_ms[i] = -1.0;
+        if (!tickets[(size_t)i]) continue;
+        const pf_status st = pf_wait(ctx, tickets[(size_t)i], -1, &latency_ms[i]);
+        if (st != PF_OK && first == PF_OK) first = st;
+    }
+    if (elapsed_s) *elapsed_s = std::chrono::duration<double>(clk::now() - t0).count();
+    return first;
+}
+
 pf_status pf_serve_stop(pf_ctx *ctx) {
     if (!ctx) return PF_EINVAL;
     ServeState *S = ctx->serve;
@@ -695,9 +896,15 @@ pf_status pf_serve_stop(pf_ctx *ctx) {
     if (S->s_copy) cudaStreamSynchronize(S->s_copy);
     {
         std::lock_guard<std::mutex> lk(S->mu);
-        for (auto &kv : S->reqs)
-            if (kv.second->state != ServeReq::DONE) finish_req(*S, *kv.second, PF_ECANCELLED);
+        for (auto &kv : S->reqs) {
+            ServeReq &q = *kv.second;
+            if (q.state == ServeReq::DONE) continue;
+            finish_req(*S, q, PF_ECANCELLED, false);
+            q.state = ServeReq::DONE;
+            S->stats.failed++;
+        }
         S->pending.clear();
+        S->active.clear();
     }
     S->cv_done.notify_all();
     {   // let every thread inside pf_wait leave before S goes away
@@ -710,12 +917,16 @@ pf_status pf_serve_stop(pf_ctx *ctx) {
     if (S->d_desc) cudaFree(S->d_desc);
     if (S->d_done) cudaFree(S->d_done);
     if (S->d_head) cudaFree(S->d_head);
+    if (S->d_last) cudaFree(S->d_last);
+    if (S->d_tail) cudaFree(S->d_tail);
+    if (S->d_exit) cudaFree(S->d_exit);
+    if (S->d_poll) cudaFree(S->d_poll);
     if (S->h_desc) cudaFreeHost(S->h_desc);
     if (S->h_items) cudaFreeHost(S->h_items);
     if (S->h_tail) cudaFreeHost(S->h_tail);
     if (S->h_stop) cudaFreeHost(S->h_stop);
     if (S->h_complete) cudaFreeHost(S->h_complete);
-    if (S->h_errs) cudaFreeHost(S->h_errs);
+    if (S->stage_mem) cudaFreeHost(S->stage_mem);
     if (S->s_copy) cudaStreamDestroy(S->s_copy);
     if (S->s_loop) cudaStreamDestroy(S->s_loop);
     if (S->ev_loop) cudaEventDestroy(S->ev_loop);

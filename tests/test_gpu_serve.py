@@ -164,3 +164,14 @@ def test_device_loop_leaves_when_idle_and_returns(pf, ctx):
     check(P2, R2, 3)
     assert pf.pf_serve_stats_get(ctx)["loop_launches"] >= 2
     pf.pf_serve_stop(ctx)
+
+
+def test_replay_open_loop_load(pf, ctx):
+    pf.pf_serve_start(ctx)
+    pool = [make_request(pf, 400 + i, n) for i, n in enumerate((1000, 4000, 12000))]
+    arrivals = np.cumsum(np.random.default_rng(1).exponential(0.002, size=30))
+    st, lat, el = pf.pf_serve_replay(ctx, [R for _, R in pool], arrivals)
+    assert st == 0 and np.all(lat > 0) and el >= arrivals[-1]
+    for P, R in pool:
+        check(P, R, 3)
+    pf.pf_serve_stop(ctx)
