@@ -103,6 +103,25 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------------
+# multi-rank helpers: replicas on their own shards, control-plane reduction
+
+def shard_start(rank, pairs_per_rank):
+    """First pair index of a rank's shard (weak scaling: every rank owns
+    pairs_per_rank consecutive pairs of the generator's pair space)."""
+    return rank * pairs_per_rank
+
+
+def max_over_ranks(value, dist=None):
+    """The slowest rank's time (MAX all-reduce on the host, no GPU data)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
 # CPU oracle baseline (also the reference arm)
 
 def oracle_step_rate(n_sample, threads=None):
@@ -217,7 +236,7 @@ def main_gpu(args):
     synth.build()
 
     n = args.pairs
-    p0 = rank * n  # this replica's shard of the pair space
+    p0 = shard_start(rank, n)
     t_gen = time.perf_counter()
     P = synth.generate(synth.SKEWED, SEED, n, m=M, E=E_HEAD, kmax=KMAX, p0=p0)
     t_gen = time.perf_counter() - t_gen
@@ -278,28 +297,6 @@ def main_gpu(args):
         if dist is not None:
             dist.barrier()
 
-    for _ in range(args.warmup):
-        step()
-    pf.pf_sync(ctx)
-    barrier()
-    clocks = Clocks(local)
-    clocks.start()
-    recs = []
-    t0, t1 = ev(), ev()
-    t0.record(stream)
-    for _ in range(args.steps):
-        step(recs)
-    t1.record(stream)
-    torch.cuda.synchronize(dev)
-    clk = clocks.stop()
-    pf.pf_sync(ctx)
-    ms = t0.elapsed_time(t1) / args.steps
-    if dist is not None:
-        tt = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    pack_ms = statistics.mean(r[0].elapsed_time(r[1]) for r in recs)
-    fv_ms = statistics.mean(r[1].elapsed_time(r[3]) for r in recs)
     if args.stage == "serve":
         out = serve_measure(pf, ctx, args.serve_seconds, SEED + 5 + rank)
         if rank == 0:
@@ -325,6 +322,24 @@ def main_gpu(args):
                   flush=True)
         pf.pf_destroy(ctx)
         return
+    for _ in range(args.warmup):
+        step()
+    pf.pf_sync(ctx)
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    recs = []
+    t0, t1 = ev(), ev()
+    t0.record(stream)
+    for _ in range(args.steps):
+        step(recs)
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    pf.pf_sync(ctx)
+    ms = max_over_ranks(t0.elapsed_time(t1) / args.steps, dist)
+    pack_ms = statistics.mean(r[0].elapsed_time(r[1]) for r in recs)
+    fv_ms = statistics.mean(r[1].elapsed_time(r[3]) for r in recs)
     if args.no_extras:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": n * world / (ms / 1000.0),
@@ -357,29 +372,21 @@ def main_gpu(args):
     ss_plain_ms = timed(lambda: pf.pf_filter_plain(ctx, 1, pairs, lens, E, E_HEAD, acc, cnt, n))
     pf.pf_sync(ctx)
 
-    # end to end through the public API: pinned host ASCII in, results out
-    def e2e_step():
-        reads.copy_(reads_h, non_blocking=True)
-        refs.copy_(refs_h, non_blocking=True)
-        step()
-        acc_h.copy_(acc, non_blocking=True)
-        cnt_h.copy_(cnt, non_blocking=True)
-        dist_h.copy_(dist_out, non_blocking=True)
-
-    e2e_step()
-    torch.cuda.synchronize(dev)
-    a, b = ev(), ev()
-    e2e_steps = max(1, min(args.steps, 5))
-    a.record(stream)
-    for _ in range(e2e_steps):
-        e2e_step()
-    b.record(stream)
-    torch.cuda.synchronize(dev)
-    e2e_ms = a.elapsed_time(b) / e2e_steps
+    # end to end through the public API: pf_run_host on pinned host ASCII,
+    # results into pinned host buffers; chunks of 1M pairs on two slots
+    # (upload of one overlapping the device work of the other), each slot's
+    # device work replayed as a CUDA graph
+    out_bufs = (acc_h.numpy(), cnt_h.numpy(), dist_h.numpy())
+    rh, fh = reads_h.numpy(), refs_h.numpy()
+    E_h = np.full(n, E_HEAD, dtype=np.int16)
+    pf.pf_run_host(ctx, 3, rh, fh, E_HEAD, length=M, E=E_h, chunk_pairs=1 << 20, out=out_bufs)
+    e2e_steps = max(1, min(args.steps, 3))
     if dist is not None:
-        tt = torch.tensor([e2e_ms], dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+        dist.barrier()
+    t_e = time.perf_counter()
+    for _ in range(e2e_steps):
+        pf.pf_run_host(ctx, 3, rh, fh, E_HEAD, length=M, E=E_h, chunk_pairs=1 << 20, out=out_bufs)
+    e2e_ms = max_over_ranks((time.perf_counter() - t_e) * 1000.0 / e2e_steps, dist)
     pf.pf_sync(ctx)
 
     serve = None if args.no_serve else serve_measure(pf, ctx, args.serve_seconds, SEED + 5 + rank)
@@ -387,19 +394,49 @@ def main_gpu(args):
     pk, pk_kind = peaks()
     stages = {"pack": pack_ms, "filter": filt_ms, "compact": compact_ms, "verify": verify_ms}
     dominant = max(stages, key=stages.get)
-    # algorithmic bytes per pair (packed input 0.75 m, outputs)
-    alg = {
+    # Algorithmic work per launch (the per-unit figures of the method, see
+    # the design doc): bytes the stage must move, and integer operations of the
+    # method counted for every word of every pair (no early exit).
+    D, Wd = 2 * E_HEAD + 1, (M + 31) // 32
+    ops_filter = 5 * D * Wd + (8 * D * Wd + Wd) + (E_HEAD + 1) * (3 * D + 1)
+    alg_bytes = {
         "pack": n * (2 * M + 2 * 3 * M / 8.0),
         "filter": n * (2 * 3 * M / 8.0 + 4 + 2 * 3),
         "compact": n * 1 + n_verified * 8,
         "verify": n_verified * (2 * 3 * M / 8.0 + 4 + 4 + 8),
     }
+    alg_ops = {
+        "pack": None,
+        "filter": n * float(ops_filter),
+        "compact": None,
+        "verify": n_verified * 20.0 * M,
+    }
+    # DRAM bytes per launch from one ncu capture of each kernel at 2M pairs
+    # (profiles/), scaled to this launch by the units processed; valid for
+    # the kernels as captured (filter<1,7,3,6>, pack_fixed, verify<u32>)
+    traffic_per_pair = {"filter": (248.020992e6 + 10.175744e6) / 2e6,
+                        "pack": 2 * (300.049152e6 + 95.794944e6) / 4e6,
+                        "verify": (249.872384e6 + 6.593024e6) / 2e6}
+    sm_mhz = clk.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+    alu_peak = 152 * 64 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # Top/s, ALU pipe
     ms_dom = stages[dominant]
-    achieved = alg[dominant] / (ms_dom / 1000.0) / 1e9
-    roof = {"kernel": dominant, "bound": "hbm", "achieved": achieved,
-            "peak": pk.get("hbm_gbs"), "unit": "GB/s",
-            "frac": achieved / pk.get("hbm_gbs"), "traffic": None,
-            "peak_source": pk_kind}
+    hbm_ach = alg_bytes[dominant] / (ms_dom / 1000.0) / 1e9
+    if alg_ops[dominant] is not None:
+        ach = alg_ops[dominant] / (ms_dom / 1000.0) / 1e12
+        roof = {"kernel": dominant, "bound": "alu", "achieved": ach, "peak": alu_peak,
+                "unit": "Tops/s", "frac": ach / alu_peak,
+                "traffic": (traffic_per_pair[dominant] * n
+                            if dominant in traffic_per_pair and M == 150 and E_HEAD == 6 else None),
+                "peak_source": "derived: 152 SMs x 64 integer ALU lanes/clk x max SM clock",
+                "ops_per_pair": ops_filter if dominant == "filter" else 20 * M,
+                "hbm_view": {"achieved_gbs": hbm_ach, "peak_gbs": pk.get("hbm_gbs"),
+                             "frac": hbm_ach / pk.get("hbm_gbs"), "peak_source": pk_kind}}
+    else:
+        roof = {"kernel": dominant, "bound": "hbm", "achieved": hbm_ach,
+                "peak": pk.get("hbm_gbs"), "unit": "GB/s", "frac": hbm_ach / pk.get("hbm_gbs"),
+                "traffic": None, "peak_source": pk_kind}
+    roof["ms_per_launch"] = ms_dom
+    roof["sm_mhz_during_step"] = sm_mhz
 
     total = n * world
     value = total / (ms / 1000.0)
@@ -419,8 +456,9 @@ def main_gpu(args):
                                "batched_over_plain": ss_plain_ms / ss_batched_ms,
                                "tuned_cfg": list(tuned[1])},
         "roofline": roof,
-        "e2e": {"value": total / (e2e_ms / 1000.0), "unit": "pairs/s",
-                "h2d_bytes_per_step": 2 * n * M,
+        "e2e": {"value": total / (e2e_ms / 1000.0), "unit": "pairs/s", "ms_per_step": e2e_ms,
+                "call": "pf_run_host (pinned host buffers, 1M-pair chunks, graph replay)",
+                "h2d_bytes_per_step": 2 * n * M + 2 * n,
                 "d2h_bytes_per_step": n * (2 + 4 + 4)},
         "gpu_launches": None,
         "serve": serve,

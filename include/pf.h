@@ -245,6 +245,27 @@ PF_API pf_status pf_filter_verify(pf_ctx *ctx, unsigned deciders, const pf_pairs
                            const int32_t *lens, const int16_t *E, int E_max,
                            uint8_t *accept, int16_t *count, int32_t *dist, int64_t n);
 
+/* ---- a7: the whole path on host buffers, chunked and graph-replayed ------ */
+
+/* Pack, filter, compact and verify n pairs held in HOST memory, chunk by
+ * chunk: two slots with their own device buffers and streams alternate,
+ * so one chunk's upload overlaps the other's device work; each slot's
+ * device work (offsets, pack, filter, compaction, verification) is captured
+ * once as a CUDA graph and replayed for every chunk of that size.  Returns
+ * when every result is in host memory.
+ *   reads, refs  host ASCII; pair p is bytes [byte_off[p], byte_off[p+1])
+ *                of both (host int64[n+1]) or, when byte_off is NULL,
+ *                bytes [p*len, (p+1)*len)
+ *   E            host int16[n], or NULL for E_max for every pair
+ *   accept, count, dist  host outputs as in pf_filter_verify
+ *   chunk_pairs  pairs per chunk (>= 1; 0 = 2^20)
+ * Page-locked host buffers are copied asynchronously; pageable ones work
+ * but serialise the copies.  Allocates its slot buffers (freed on return). */
+PF_API pf_status pf_run_host(pf_ctx *ctx, unsigned deciders, const uint8_t *reads,
+                             const uint8_t *refs, const int64_t *byte_off, int len,
+                             const int16_t *E, int E_max, uint8_t *accept, int16_t *count,
+                             int32_t *dist, int64_t n, int64_t chunk_pairs);
+
 /* ---- a8: serving (continuous batching over a device-resident loop) ------ */
 
 /* The accelerator of Ch. 4 streams pairs through its filtering units and

@@ -21,7 +21,7 @@ __all__ = [
     "pf_compact", "pf_verify", "pf_filter_verify", "library_path", "load", "pack_pairs",
     "pf_kernel_configs", "pf_tune_set", "pf_tune_get", "pf_tune", "pf_compact_noalloc",
     "ServeConfig", "Request", "pf_serve_start", "pf_submit", "pf_poll", "pf_wait",
-    "pf_serve_resume", "pf_serve_stats_get", "pf_serve_stop", "pf_serve_replay",
+    "pf_serve_resume", "pf_serve_stats_get", "pf_serve_stop", "pf_serve_replay", "pf_run_host",
 ]
 
 PF_SNEAKYSNAKE = 1
@@ -114,6 +114,7 @@ def load():
         "pf_serve_resume": [P],
         "pf_serve_stats_get": [P, ctypes.POINTER(ServeStats)],
         "pf_serve_stop": [P],
+        "pf_run_host": [P, U, P, P, P, I, P, I, P, P, P, I64, I64],
         "pf_serve_replay": [P, P, I, P, I, P, ctypes.POINTER(ctypes.c_double)],
         "pf_tune_set": [P, U, I, I, I],
         "pf_tune_get": [P, U, I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
@@ -482,3 +483,29 @@ def pf_serve_replay(ctx, pool, arrival_s):
                                 ctypes.c_void_p(t.ctypes.data), len(t),
                                 ctypes.c_void_p(lat.ctypes.data), ctypes.byref(el))
     return st, lat[:len(t)], el.value
+
+
+def pf_run_host(ctx, deciders, reads, refs, E_max, byte_off=None, length=0, E=None,
+                chunk_pairs=0, out=None):
+    """Whole path on host numpy arrays, chunked and graph-replayed on the
+    device.  Returns (accept[slots, n], count[slots, n], dist[n])."""
+    import numpy as np
+    reads = np.ascontiguousarray(reads, dtype=np.uint8)
+    refs = np.ascontiguousarray(refs, dtype=np.uint8)
+    if byte_off is not None:
+        byte_off = np.ascontiguousarray(byte_off, dtype=np.int64)
+        n = len(byte_off) - 1
+    else:
+        n = reads.size // length if length else 0
+    slots = 2 if deciders == 3 else 1
+    if out is None:
+        out = (np.zeros(slots * max(n, 1), np.uint8), np.zeros(slots * max(n, 1), np.int16),
+               np.zeros(max(n, 1), np.int32))
+    acc, cnt, dist = out
+    ptr = lambda a: ctypes.c_void_p(a.ctypes.data) if a is not None else None
+    if E is not None:
+        E = np.ascontiguousarray(E, dtype=np.int16)
+    _check(load().pf_run_host(ctx.handle, int(deciders), ptr(reads), ptr(refs), ptr(byte_off),
+                              int(length), ptr(E), int(E_max), ptr(acc), ptr(cnt), ptr(dist),
+                              int(n), int(chunk_pairs)), ctx.handle)
+    return acc[:slots * n].reshape(slots, n), cnt[:slots * n].reshape(slots, n), dist[:n]

@@ -108,6 +108,14 @@ dist_fill_rejected_kernel(const uint8_t *accept, const int16_t *E, int E_max, in
     }
 }
 
+cudaError_t launch_dist_fill(const uint8_t *accept, const int16_t *E, int E_max, int64_t n,
+                             int32_t *dist, int sms, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t fb = std::min<int64_t>((n + 255) / 256, (int64_t)sms * 16);
+    dist_fill_rejected_kernel<<<(unsigned)fb, 256, 0, st>>>(accept, E, E_max, n, dist);
+    return cudaGetLastError();
+}
+
 }  // namespace pf
 
 // ---------------------------------------------------------------------------
@@ -548,9 +556,8 @@ pf_status pf_filter_verify(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs
     st = ctx->cuda(launch_compact(accept, n, s.idx, s.n_idx, s.tiles, ctx->stream),
                    "compact launch");
     if (st != PF_OK) return st;
-    const int64_t fb = std::min<int64_t>((n + 255) / 256, (int64_t)ctx->sms * 16);
-    dist_fill_rejected_kernel<<<(unsigned)fb, 256, 0, ctx->stream>>>(accept, E, E_max, n, dist);
-    st = ctx->cuda(cudaGetLastError(), "fill launch");
+    st = ctx->cuda(launch_dist_fill(accept, E, E_max, n, dist, ctx->sms, ctx->stream),
+                   "fill launch");
     if (st != PF_OK) return st;
     return ctx->cuda(launch_verify(to_view(pairs), lens, E, E_max, s.idx, s.n_idx, n, dist,
                                    ctx->d_err, ctx->sms, ctx->stream),

@@ -1,0 +1,61 @@
+"""pf_run_host: the whole path on host buffers, chunked over two slots and
+replayed as CUDA graphs, bit-exact with the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pf():
+    from paper_1910_03936_gb300 import build
+    build.build()
+    import paper_1910_03936_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(pf):
+    c = pf.pf_create(0)
+    yield c
+    pf.pf_destroy(c)
+
+
+def expected(P, deciders):
+    acc, cnt = oracle.filter_batch(P, deciders=deciders)
+    vb = oracle.verify_batch(P)
+    return acc, cnt, np.where(acc[0] == 1, vb, P.E.astype(np.int32) + 1)
+
+
+@pytest.mark.parametrize("chunk", [1000, 4096, 0])
+@pytest.mark.parametrize("dec", [3, 1])
+def test_ragged_chunks(pf, ctx, chunk, dec):
+    P = synth.generate(synth.MIXED, 21, 10007)
+    acc, cnt, dist = pf.pf_run_host(ctx, dec, P.reads, P.refs, int(P.E.max()),
+                                    byte_off=P.read_off, E=P.E, chunk_pairs=chunk)
+    oa, oc, od = expected(P, dec)
+    assert np.array_equal(cnt, oc) and np.array_equal(acc, oa)
+    assert np.array_equal(dist, od)
+
+
+@pytest.mark.parametrize("chunk", [777, 5000])
+def test_fixed_length_uniform_E(pf, ctx, chunk):
+    P = synth.generate(synth.SKEWED, 22, 9001, m=150, E=6)
+    acc, cnt, dist = pf.pf_run_host(ctx, 3, P.reads, P.refs, 6, length=150, chunk_pairs=chunk)
+    oa, oc, od = expected(P, 3)
+    assert np.array_equal(cnt, oc) and np.array_equal(acc, oa)
+    assert np.array_equal(dist, od)
+
+
+def test_pinned_host_buffers(pf, ctx):
+    import torch
+    P = synth.generate(synth.SKEWED_ALL, 23, 3000, m=250, E=25, kmax=100)
+    reads = torch.from_numpy(P.reads).pin_memory().numpy()
+    refs = torch.from_numpy(P.refs).pin_memory().numpy()
+    acc, cnt, dist = pf.pf_run_host(ctx, 3, reads, refs, 25, length=250, E=P.E, chunk_pairs=1024)
+    oa, oc, od = expected(P, 3)
+    assert np.array_equal(cnt, oc) and np.array_equal(acc, oa)
+    assert np.array_equal(dist, od)
