@@ -215,6 +215,104 @@ def serve_measure(pf, ctx, seconds_per_load, seed):
 
 
 # ---------------------------------------------------------------------------
+# the other configurations (their own lines; the default line is the
+# 150 bp, E = 6 workload above)
+
+def run_other_workload(args):
+    import torch
+    import synth
+    import paper_1910_03936_gb300 as pf
+    from paper_1910_03936_gb300 import build as pfbuild
+    pfbuild.build()
+    synth.build()
+    dev = torch.device("cuda", 0)
+    ctx = pf.pf_create(0)
+    stream = torch.cuda.current_stream(dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps):
+        for _ in range(args.warmup):
+            fn()
+        a, b = ev(), ev()
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / reps
+
+    w = args.workload
+    if w == "cfg1":   # plain SneakySnake, 100k pairs of 100 bp from ASCII, E = 5
+        P = synth.generate(synth.UNIFORM, 0x5EED0000, 100_000, m=100, E=5, kmax=20)
+        fixed, Emax, kind = 100, 5, "uniform"
+    elif w == "cfg3":  # 50M pairs, 100/150/250 bp, E = round(r*len)
+        P = synth.generate(synth.MIXED, 0x5EED0003, 50_000_000, kmax=60)
+        fixed, Emax, kind = None, int(P.E.max()), "mixed"
+    else:              # cfg4: 10M pairs of 250 bp, E = 25
+        P = synth.generate(synth.SKEWED_ALL, 0x5EED0004, 10_000_000, m=250, E=25, kmax=100)
+        fixed, Emax, kind = 250, 25, "skewed_all"
+    n = P.n
+    reads_h = torch.from_numpy(P.reads).pin_memory()
+    refs_h = torch.from_numpy(P.refs).pin_memory()
+    reads, refs = reads_h.to(dev), refs_h.to(dev)
+    lens = torch.from_numpy(P.lens).to(dev)
+    E = torch.from_numpy(P.E).to(dev)
+    if fixed:
+        W = (fixed + 31) // 32
+        rd = pf.Seqs.empty(n * W, dev, stride_words=W)
+        rf = pf.Seqs.empty(n * W, dev, stride_words=W)
+        pack = lambda: (pf.pf_pack_fixed(ctx, reads, n, fixed, rd),
+                        pf.pf_pack_fixed(ctx, refs, n, fixed, rf))
+    else:
+        wo, total = pf.pf_pack_layout(P.read_off)
+        bo_d = torch.from_numpy(P.read_off).to(dev)
+        wo_d = torch.from_numpy(wo).to(dev)
+        rd = pf.Seqs.empty(total, dev, word_off=wo_d)
+        rf = pf.Seqs.empty(total, dev, word_off=wo_d)
+        pack = lambda: (pf.pf_pack(ctx, reads, bo_d, wo_d, rd), pf.pf_pack(ctx, refs, bo_d, wo_d, rf))
+    pairs = pf.Pairs(rd, rf)
+    pack()
+    acc = torch.zeros(2 * n, dtype=torch.uint8, device=dev)
+    cnt = torch.zeros(2 * n, dtype=torch.int16, device=dev)
+    dist = torch.zeros(n, dtype=torch.int32, device=dev)
+    out = {"workload": w, "pairs": n, "recipe": kind, "E_max": Emax}
+    reps = max(1, args.steps)
+    out["pack_ms"] = timed(pack, reps)
+    if w == "cfg1":
+        out["ss_plain_ms"] = timed(lambda: pf.pf_filter_plain(ctx, 1, pairs, lens, E, 5, acc, cnt, n), reps)
+        out["ss_batched_ms"] = timed(lambda: pf.pf_filter(ctx, 1, pairs, lens, E, 5, acc, cnt, n), reps)
+        step = lambda: (pack(), pf.pf_filter(ctx, 1, pairs, lens, E, 5, acc, cnt, n))
+        out["step"] = "pack + batched SneakySnake"
+    else:
+        for e in range(0, min(Emax, 15) + 1):
+            pf.pf_tune(ctx, 3, pairs, lens, e, n=min(n, 1_000_000), reps=1)
+        out["filter_ms"] = timed(lambda: pf.pf_filter(ctx, 3, pairs, lens, E, Emax, acc, cnt, n), reps)
+        out["filter_verify_ms"] = timed(
+            lambda: pf.pf_filter_verify(ctx, 3, pairs, lens, E, Emax, acc, cnt, dist, n), reps)
+        out["verify_all_ms"] = timed(
+            lambda: pf.pf_verify(ctx, pairs, lens, E, Emax, None, None, dist, n), reps)
+        step = lambda: (pack(), pf.pf_filter_verify(ctx, 3, pairs, lens, E, Emax, acc, cnt, dist, n))
+        out["step"] = "pack + batched filter (both deciders) + compact + verify"
+    step_ms = timed(step, reps)
+    out["ms_per_step"] = step_ms
+    out["value"] = n / (step_ms / 1000.0)
+    out["unit"] = "pairs/s"
+    if w == "cfg3":  # chunked host pipeline, graph replay, pinned host buffers
+        import time
+        acc_h = torch.empty(2 * n, dtype=torch.uint8).pin_memory().numpy()
+        cnt_h = torch.empty(2 * n, dtype=torch.int16).pin_memory().numpy()
+        dist_h = torch.empty(n, dtype=torch.int32).pin_memory().numpy()
+        args_rh = (ctx, 3, reads_h.numpy(), refs_h.numpy(), Emax)
+        kw = dict(byte_off=P.read_off, E=P.E, chunk_pairs=1 << 21, out=(acc_h, cnt_h, dist_h))
+        pf.pf_run_host(*args_rh, **kw)
+        t = time.perf_counter()
+        pf.pf_run_host(*args_rh, **kw)
+        out["e2e_host_pipeline_pairs_s"] = n / (time.perf_counter() - t)
+    print(json.dumps(out), flush=True)
+    pf.pf_destroy(ctx)
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 
 def main_gpu(args):
@@ -499,10 +597,14 @@ def main():
                     help="time one filter kernel instead of the step (profiling)")
     ap.add_argument("--deciders", type=int, default=3)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--workload", default="headline", choices=["headline", "cfg1", "cfg3", "cfg4"],
+                    help="other configurations, each on its own line")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "headline":
+        run_other_workload(args)
     else:
         main_gpu(args)
 
