@@ -139,8 +139,6 @@ struct PairFilter {
         const Word3 F = Fw;
         Fw = load_word<L>(pv.ref, fb, w + 1, W);  // prefetch the next reference word
         uint32_t M[NS];
-        const uint32_t valid =
-            (w == W - 1 && (m & 31)) ? ((1u << (m & 31)) - 1u) : 0xffffffffu;
 
         // ---- map words of this lane's diagonals
         Word3 A, B;
@@ -170,7 +168,13 @@ struct PairFilter {
                 shi = shr_pair(A.hi, B.hi, d);
                 snm = shr_pair(A.nm, B.nm, d);
             }
-            M[k] = ((F.lo ^ slo) | (F.hi ^ shi) | F.nm | snm) & valid;
+            M[k] = (F.lo ^ slo) | (F.hi ^ shi) | F.nm | snm;
+        }
+        if (w == W - 1 && (m & 31)) {  // columns >= m of the last word are not cells
+            const uint32_t valid = (1u << (m & 31)) - 1u;
+#pragma unroll
+            for (int k = 0; k < NS; ++k)
+                if (live(k, g)) M[k] &= valid;
         }
 
         // ---- SneakySnake steps inside this word

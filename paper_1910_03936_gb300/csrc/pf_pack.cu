@@ -43,8 +43,8 @@ pack_ragged_kernel(const uint8_t *ascii, const int64_t *byte_off, const int64_t 
 // Block b packs global words [256 b, 256 b + 256); one 64-bit division per
 // block locates its first word, threads step from there.
 __global__ void __launch_bounds__(kPackThreads)
-pack_fixed_kernel(const uint8_t *ascii, int64_t nseq, int len, int W, uint32_t *lo,
-                  uint32_t *hi, uint32_t *nm, unsigned *err) {
+pack_fixed_kernel(const uint8_t *ascii, int64_t nseq, int len, int W, uint32_t wmagic,
+                  uint32_t *lo, uint32_t *hi, uint32_t *nm, unsigned *err) {
     __shared__ int64_t s_first;
     __shared__ int w_first;
     const int64_t total = nseq * (int64_t)W;
@@ -56,9 +56,12 @@ pack_fixed_kernel(const uint8_t *ascii, int64_t nseq, int len, int W, uint32_t *
     __syncthreads();
     const int64_t gw = gw0 + threadIdx.x;
     if (gw >= total) return;
-    const int local = w_first + (int)threadIdx.x;
-    const int64_t s = s_first + local / W;
-    const int w = local % W;
+    const unsigned local = (unsigned)w_first + threadIdx.x;
+    // local / W by multiply-high when wmagic = ceil(2^32 / W) is exact for
+    // every local < W + 256 (W <= 4096), else by division
+    const unsigned q = wmagic ? __umulhi(local, wmagic) : local / (unsigned)W;
+    const int64_t s = s_first + q;
+    const int w = (int)(local - q * (unsigned)W);
     pack_word(ascii + s * (int64_t)len, len, w, lo + gw, hi + gw, nm + gw, err);
 }
 
@@ -82,8 +85,10 @@ cudaError_t launch_pack_fixed(const uint8_t *ascii, int64_t nseq, int len, uint3
     if (total <= 0) return cudaSuccess;
     (void)sms;
     const int64_t blocks = (total + kPackThreads - 1) / kPackThreads;
-    pack_fixed_kernel<<<(unsigned)blocks, kPackThreads, 0, st>>>(ascii, nseq, len, W, lo, hi,
-                                                                nm, err);
+    const uint32_t wmagic =
+        (W <= 4096) ? (uint32_t)((((uint64_t)1 << 32) + (uint64_t)W - 1) / (uint64_t)W) : 0u;
+    pack_fixed_kernel<<<(unsigned)blocks, kPackThreads, 0, st>>>(ascii, nseq, len, W, wmagic,
+                                                                lo, hi, nm, err);
     return cudaGetLastError();
 }
 

@@ -13,12 +13,21 @@ namespace pf {
 //   n 0x6e -> 111 (bit 1, bit 2, bit 3).
 // low code bit = bit1 ^ bit2, high code bit = bit2, N = bit3.
 //
-// Gather: for x with one flag bit at bit s of each byte, x * (0x10204080 >>
-// s) puts the flag of byte i at bit 28 + i and every other partial product
-// on a distinct lower bit or above bit 31, so bits 28..31 are the 4 flags.
+// Eight bytes are handled per step.  With a = bytes 0..3 and b = bytes
+// 4..7 of the step, Y keeps the low nibble of byte j of a in nibble 2j and
+// the low nibble of byte j of b in nibble 2j+1, so a flag bit at bit S of
+// every byte of a and b sits at bits S + 8j (a) and S + 8j + 4 (b) of Y.
+// Multiplying the masked flags by sum_j 2^(24 - 7j - S) sends both flags of
+// byte j (the a one and the b one) to bits 24 + j and 28 + j; every other
+// partial product lands on a distinct bit below 24 or beyond bit 31, so no
+// carry reaches bits 24..31, which then hold the 8 flags in byte order.
+__device__ __forceinline__ uint32_t interleave_nibbles(uint32_t a, uint32_t b) {
+    return (a & 0x0f0f0f0fu) | ((b << 4) & 0xf0f0f0f0u);
+}
+
 template <int S>
-__device__ __forceinline__ uint32_t gather4(uint32_t x) {
-    return (x & (0x01010101u << S)) * (0x10204080u >> S);
+__device__ __forceinline__ uint32_t gather8(uint32_t y) {
+    return (y & (0x11111111u << S)) * (0x01020408u >> S);
 }
 
 // Canonical lower-case letter per 3-bit pattern (bits 1..3 of the byte),
@@ -27,20 +36,25 @@ __device__ __forceinline__ uint32_t gather4(uint32_t x) {
 constexpr uint32_t kCanonLo = 0x67746361u;  // g t c a
 constexpr uint32_t kCanonHi = 0x6e000000u;  // n . . .
 
-// Per-byte classification of four bytes against the canonical table:
-// returns a nonzero word iff some byte outside `pad` is not A/C/G/T/N.
-__device__ __forceinline__ uint32_t invalid4(uint32_t v, uint32_t pad) {
-    const uint32_t x = (v >> 1) & 0x07070707u;          // pattern per byte
-    const uint32_t y = x | (x >> 4);                    // byte0 = p0|p1<<4, byte2 = p2|p3<<4
-    const uint32_t sel = __byte_perm(y, 0u, 0x0020u);   // nibbles p0 p1 p2 p3
-    const uint32_t canon = __byte_perm(kCanonLo, kCanonHi, sel);
-    return (canon ^ (v | 0x20202020u)) & ~pad;
+// Nonzero iff one of the 8 bytes of (a, b) is not A/C/G/T/N (either case).
+// The patterns of Y, one per nibble, select the canonical letters of bytes
+// (a0 b0 a1 b1) and (a2 b2 a3 b3); the bytes are interleaved the same way.
+__device__ __forceinline__ uint32_t invalid8(uint32_t a, uint32_t b, uint32_t y) {
+    const uint32_t z = (y >> 1) & 0x77777777u;
+    const uint32_t c0 = __byte_perm(kCanonLo, kCanonHi, z);
+    const uint32_t c1 = __byte_perm(kCanonLo, kCanonHi, z >> 16);
+    const uint32_t i0 = __byte_perm(a, b, 0x5140u);
+    const uint32_t i1 = __byte_perm(a, b, 0x7362u);
+    return (c0 ^ (i0 | 0x20202020u)) | (c1 ^ (i1 | 0x20202020u));
 }
 
-// Per-byte exact classification, for words that hold an invalid byte.
-__device__ __forceinline__ void slow_word(const uint32_t *vals, int vb, uint32_t *lo,
+// Per-byte exact classification of the first vb bytes, for words in which
+// the fast test saw a byte outside A/C/G/T/N.  Returns whether such a byte
+// lies among the first vb (bytes past vb are N and never an error).
+__device__ __forceinline__ bool slow_word(const uint32_t *vals, int vb, uint32_t *lo,
                                           uint32_t *hi, uint32_t *nm) {
     uint32_t olo = 0u, ohi = 0u, onm = 0u;
+    bool found = false;
     for (int b = 0; b < 32; ++b) {
         const uint32_t c = (vals[b >> 2] >> (8 * (b & 3))) & 0xffu;
         const uint32_t l = c | 0x20u;
@@ -50,7 +64,10 @@ __device__ __forceinline__ void slow_word(const uint32_t *vals, int vb, uint32_t
         else if (l == 0x63u) code = 1;
         else if (l == 0x67u) code = 2;
         else if (l == 0x74u) code = 3;
-        else code = 4;  // N and every invalid byte
+        else {
+            code = 4;
+            found |= (l != 0x6eu);
+        }
         if (code == 4) onm |= 1u << b;
         else {
             if (code & 1) olo |= 1u << b;
@@ -60,9 +77,14 @@ __device__ __forceinline__ void slow_word(const uint32_t *vals, int vb, uint32_t
     *lo = olo;
     *hi = ohi;
     *nm = onm;
+    return found;
 }
 
-// Pack word w of a sequence whose bytes start at `src` (len bytes).
+// Pack word w of a sequence whose bytes start at `src` (len bytes).  All 32
+// byte slots go through the fast path, including those past the end: 4-byte
+// words wholly past the end are not read and count as "NNNN"; a partly
+// valid word keeps its other bytes, so a byte past the end that is not a base
+// only sends the word to the exact path.
 template <typename L = LdNC>
 __device__ __forceinline__ void pack_word(const uint8_t *src, int len, int w, uint32_t *lo,
                                           uint32_t *hi, uint32_t *nm, unsigned *err) {
@@ -76,34 +98,29 @@ __device__ __forceinline__ void pack_word(const uint8_t *src, int len, int w, ui
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         const uintptr_t wa = reinterpret_cast<uintptr_t>(aw + k);
-        u[k] = (wa < end) ? L::ld(aw + k) : 0u;
+        u[k] = (wa < end) ? L::ld(aw + k) : 0x4e4e4e4eu;
     }
     uint32_t v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __funnelshift_r(u[i], u[i + 1], sh);
     uint32_t olo = 0u, ohi = 0u, onm = 0u, bad = 0u;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        v[i] = __funnelshift_r(u[i], u[i + 1], sh);
-        const int first = 4 * i;
-        uint32_t pad;
-        if (first + 4 <= vb) pad = 0u;
-        else if (first >= vb) pad = 0xffffffffu;
-        else pad = 0xffffffffu << (8 * (vb - first));
-        bad |= invalid4(v[i], pad);
-        const uint32_t t = v[i] ^ (v[i] >> 1);  // bit 1 = bit1 ^ bit2
-        const int up = 28 - first;          // flags of bytes first..first+3
-        const uint32_t keep = 0xfu << first;
-        olo |= (gather4<1>(t) >> up) & keep;
-        ohi |= (gather4<2>(v[i]) >> up) & keep;
-        onm |= (gather4<3>(v[i]) >> up) & keep;
+    for (int i = 0; i < 4; ++i) {
+        const uint32_t y = interleave_nibbles(v[2 * i], v[2 * i + 1]);
+        bad |= invalid8(v[2 * i], v[2 * i + 1], y);
+        const uint32_t t = y ^ (y >> 1);  // bit 1 of each nibble: bit1 ^ bit2
+        const uint32_t keep = 0xffu << (8 * i);
+        olo |= (gather8<1>(t) >> (24 - 8 * i)) & keep;
+        ohi |= (gather8<2>(y) >> (24 - 8 * i)) & keep;
+        onm |= (gather8<3>(y) >> (24 - 8 * i)) & keep;
     }
     if (bad) {
-        slow_word(v, vb, lo, hi, nm);
-        atomicOr(err, ERR_BYTES);
+        if (slow_word(v, vb, lo, hi, nm)) atomicOr(err, ERR_BYTES);
         return;
     }
     const uint32_t vmask = (vb >= 32) ? 0xffffffffu : ((1u << vb) - 1u);
-    onm = (onm & vmask) | ~vmask;  // bytes past the end are N
-    *lo = olo & ~onm;              // N carries code 00
+    onm |= ~vmask;      // bytes past the end are N
+    *lo = olo & ~onm;   // N carries code 00
     *hi = ohi & ~onm;
     *nm = onm;
 }
