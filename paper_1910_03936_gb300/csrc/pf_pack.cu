@@ -24,6 +24,7 @@ pack_ragged_kernel(const uint8_t *ascii, const int64_t *byte_off, const int64_t 
         boff[i] = byte_off[s0 + i];
     }
     __syncthreads();
+    const uint8_t *lim = ascii + __ldg(byte_off + nseq);
     const int64_t base = woff[0];
     const int total = (int)(woff[ns] - base);
     for (int j = threadIdx.x; j < total; j += blockDim.x) {
@@ -35,7 +36,7 @@ pack_ragged_kernel(const uint8_t *ascii, const int64_t *byte_off, const int64_t 
         }
         const int w = (int)(gw - woff[l]);
         const int len = (int)(boff[l + 1] - boff[l]);
-        pack_word(ascii + boff[l], len, w, lo + gw, hi + gw, nm + gw, err);
+        pack_word(ascii + boff[l], len, w, lo + gw, hi + gw, nm + gw, err, lim);
     }
 }
 
@@ -62,7 +63,8 @@ pack_fixed_kernel(const uint8_t *ascii, int64_t nseq, int len, int W, uint32_t w
     const unsigned q = wmagic ? __umulhi(local, wmagic) : local / (unsigned)W;
     const int64_t s = s_first + q;
     const int w = (int)(local - q * (unsigned)W);
-    pack_word(ascii + s * (int64_t)len, len, w, lo + gw, hi + gw, nm + gw, err);
+    pack_word(ascii + s * (int64_t)len, len, w, lo + gw, hi + gw, nm + gw, err,
+              ascii + nseq * (int64_t)len);
 }
 
 }  // namespace

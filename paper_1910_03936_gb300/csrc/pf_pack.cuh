@@ -81,24 +81,33 @@ __device__ __forceinline__ bool slow_word(const uint32_t *vals, int vb, uint32_t
 }
 
 // Pack word w of a sequence whose bytes start at `src` (len bytes).  All 32
-// byte slots go through the fast path, including those past the end: 4-byte
-// words wholly past the end are not read and count as "NNNN"; a partly
-// valid word keeps its other bytes, so a byte past the end that is not a base
-// only sends the word to the exact path.
+// byte slots go through the fast path, including those past the end, which
+// are then forced to N.  `lim` is one past the last byte of the whole input
+// buffer: a word whose 36-byte window lies below it (rounded up to 4 bytes)
+// reads its window unguarded, so bytes past the end of the sequence are the
+// next sequence's; otherwise 4-byte words wholly past the end are not read
+// and count as "NNNN".  A byte past the end that is not a base only sends
+// the word to the exact path.
 template <typename L = LdNC>
 __device__ __forceinline__ void pack_word(const uint8_t *src, int len, int w, uint32_t *lo,
-                                          uint32_t *hi, uint32_t *nm, unsigned *err) {
+                                          uint32_t *hi, uint32_t *nm, unsigned *err,
+                                          const uint8_t *lim) {
     const int b0 = 32 * w;
     const int vb = min(32, len - b0);  // valid bytes in this word, >= 1
     const uintptr_t a = reinterpret_cast<uintptr_t>(src + b0);
     const uint32_t *aw = reinterpret_cast<const uint32_t *>(a & ~uintptr_t(3));
     const unsigned sh = 8u * unsigned(a & 3u);
-    const uintptr_t end = a + (uintptr_t)vb;  // one past the last valid byte
     uint32_t u[9];
+    if (reinterpret_cast<uintptr_t>(aw + 9) <= ((reinterpret_cast<uintptr_t>(lim) + 3u) & ~uintptr_t(3))) {
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        const uintptr_t wa = reinterpret_cast<uintptr_t>(aw + k);
-        u[k] = (wa < end) ? L::ld(aw + k) : 0x4e4e4e4eu;
+        for (int k = 0; k < 9; ++k) u[k] = L::ld(aw + k);
+    } else {
+        const uintptr_t end = a + (uintptr_t)vb;  // one past the last valid byte
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const uintptr_t wa = reinterpret_cast<uintptr_t>(aw + k);
+            u[k] = (wa < end) ? L::ld(aw + k) : 0x4e4e4e4eu;
+        }
     }
     uint32_t v[8];
 #pragma unroll

@@ -240,6 +240,7 @@ __global__ void __launch_bounds__(kServeThreads) serve_loop_kernel(ServeDevice s
         __syncthreads();
         const int64_t wbase = s_woff[0];
         const int wtot = (int)(s_woff[np] - wbase);
+        const int64_t btot = __ldcg(d.byte_off + d.n) - b00;  // the request's bytes
         for (int j = threadIdx.x; j < wtot; j += blockDim.x) {
             const int64_t gw = wbase + j;
             int l = 0, r = np - 1;
@@ -250,8 +251,10 @@ __global__ void __launch_bounds__(kServeThreads) serve_loop_kernel(ServeDevice s
             const int w = (int)(gw - s_woff[l]);
             const int len = (int)(s_boff[l + 1] - s_boff[l]);
             if (w >= (len + 31) / 32) continue;  // gap word between sequences
-            pack_word<LdCG>(d.reads + s_boff[l], len, w, d.rlo + gw, d.rhi + gw, d.rnm + gw, d.err);
-            pack_word<LdCG>(d.refs + s_boff[l], len, w, d.flo + gw, d.fhi + gw, d.fnm + gw, d.err);
+            pack_word<LdCG>(d.reads + s_boff[l], len, w, d.rlo + gw, d.rhi + gw, d.rnm + gw, d.err,
+                            d.reads + btot);
+            pack_word<LdCG>(d.refs + s_boff[l], len, w, d.flo + gw, d.fhi + gw, d.fnm + gw, d.err,
+                            d.refs + btot);
         }
         __syncthreads();
 

@@ -38,18 +38,64 @@ struct Bits<uint64_t> {
     static __device__ __forceinline__ int popc(uint64_t x) { return __popcll(x); }
 };
 
-// Window of a read plane starting at bit s (may be negative): bits
-// [s, s + 8*sizeof(U)).  wm1, w0, w1, w2 are read words q-1 .. q+2 with
-// q = floor(s / 32) + 1 ... passed as the three/four words that cover it.
+// 0 or ~0: bit t of x, spread over the word.
+__device__ __forceinline__ uint32_t bcast(uint32_t x, int t) {
+    return (uint32_t)((int32_t)(x << (31 - t)) >> 31);
+}
+
 template <typename U>
-__device__ __forceinline__ U window(uint32_t a, uint32_t b, uint32_t c, unsigned r) {
+__device__ __forceinline__ U spread(uint32_t b) {
+    if constexpr (sizeof(U) == 4) return b;
+    else return ((uint64_t)b << 32) | b;
+}
+
+// The read's three planes from bit 32*fw - E on: x0 covers the first 32
+// bits, x1 the next 32, x2 the 32 after (used by 64-bit bands only).
+struct ReadWin {
+    uint32_t lo0, lo1, lo2, hi0, hi1, hi2, nm0, nm1, nm2;
+};
+
+// Bits [t, t + |U|) of the window.
+template <typename U>
+__device__ __forceinline__ U win(uint32_t x0, uint32_t x1, uint32_t x2, int t) {
     if constexpr (sizeof(U) == 4) {
-        return __funnelshift_r(a, b, r);
+        return __funnelshift_r(x0, x1, (unsigned)t);
     } else {
-        const uint64_t lo = __funnelshift_r(a, b, r);
-        const uint64_t hi = __funnelshift_r(b, c, r);
-        return lo | (hi << 32);
+        return ((uint64_t)__funnelshift_r(x1, x2, (unsigned)t) << 32) |
+               __funnelshift_r(x0, x1, (unsigned)t);
     }
+}
+
+// One DP column: reference base at bit t of the reference word f, band rows
+// read from the window at offset t.  VP keeps the bottom stand-in bit set;
+// bit 0 of the new top-row differences goes to the top of accP / accM.
+template <typename U>
+__device__ __forceinline__ void column(const ReadWin &r, const Word3 &f, int t, U store_mask,
+                                       U bottom, U &VP, U &VN, uint32_t &accP,
+                                       uint32_t &accM) {
+    const U mlo = spread<U>(bcast(f.lo, t));
+    const U mhi = spread<U>(bcast(f.hi, t));
+    const U fn = spread<U>(bcast(f.nm, t));
+    const U wlo = win<U>(r.lo0, r.lo1, r.lo2, t);
+    const U whi = win<U>(r.hi0, r.hi1, r.hi2, t);
+    const U wnm = win<U>(r.nm0, r.nm1, r.nm2, t);
+    // Eq bit q: read base of row j-E+q equals the reference base, neither N.
+    // Bits above the band (q > 2E) only ever influence higher bits (carries
+    // and the left shifts run upwards), and the stored vectors drop them.
+    const U Eq = ~((wlo ^ mlo) | (whi ^ mhi) | wnm | fn);
+    const U Pv = VP;
+    const U X = Eq | VN;
+    const U D0 = (((X & Pv) + Pv) ^ Pv) | X;
+    U Ph = VN | ~(D0 | Pv);
+    U Mh = Pv & D0;
+    Ph = (Ph << 1) | U(1);  // +1 enters above the top row
+    Mh = Mh << 1;
+    const U nPv = Mh | ~(D0 | Ph);
+    const U nMv = Ph & D0;
+    accP = __funnelshift_r(accP, (uint32_t)nPv, 1);
+    accM = __funnelshift_r(accM, (uint32_t)nMv, 1);
+    VP = ((nPv >> 1) & store_mask) | bottom;
+    VN = (nMv >> 1) & store_mask;
 }
 
 template <typename U, typename L = LdNC>
@@ -57,61 +103,66 @@ __device__ __forceinline__ int verify_pair(const PairsView &pv, int64_t p, int m
     if (m == 0) return 0;
     const int W = (m + 31) >> 5;
     const int64_t rb = pv.read.template start<L>(p), fb = pv.ref.template start<L>(p);
-    const int BW = 2 * E + 1;                       // band width (bits used)
-    const U band_mask = (BW >= (int)(8 * sizeof(U))) ? ~U(0) : ((U(1) << BW) - 1);
     const U store_mask = (U(1) << (2 * E)) - 1;     // 2E stored differences
-    const U bottom = U(1) << (2 * E);
+    const U bottom = U(1) << (2 * E);               // +1 stand-in of row j+E
 
     // column 0: rows -E..E hold |i|; differences -1 for rows -E+1..0,
     // +1 for rows 1..E
     U VN = (U(1) << E) - 1;
-    U VP = store_mask & ~VN;
+    U VP = (store_mask & ~VN) | bottom;
     int T = E;
 
-    // Read window: bits [s, s+|U|) with s = j - E - 1 at column j.  Keep the
-    // read words q0 .. q0+2 where q0 = floor(s / 32).
-    int s = -E;                   // s for column j = 1
-    int q0 = (s >= 0) ? (s >> 5) : -1;
-    Word3 r0 = load_word<L>(pv.read, rb, q0, W);
-    Word3 r1 = load_word<L>(pv.read, rb, q0 + 1, W);
-    Word3 r2 = load_word<L>(pv.read, rb, q0 + 2, W);
-    Word3 f = load_word<L>(pv.ref, fb, 0, W);
-
-    for (int j = 1; j <= m; ++j, ++s) {
-        const int q = s >> 5;    // arithmetic shift: floor for negatives
-        if (q != q0) {           // the window moved into the next word
-            q0 = q;
-            r0 = r1;
-            r1 = r2;
-            r2 = load_word<L>(pv.read, rb, q0 + 2, W);
+    // Reference word fw holds columns j = 32 fw + 1 + t (t = 0..31), whose
+    // band starts at read bit s = j - E - 1 = 32 fw - E + t.  Read words
+    // fw-1 .. fw+2 cover every window of the word.
+    const unsigned rs = 32u - (unsigned)E;
+    Word3 ra = load_word<L>(pv.read, rb, -1, W);
+    Word3 rb0 = load_word<L>(pv.read, rb, 0, W);
+    Word3 rc = load_word<L>(pv.read, rb, 1, W);
+    Word3 rd;
+    if constexpr (sizeof(U) == 8) rd = load_word<L>(pv.read, rb, 2, W);
+    for (int fw = 0; fw < W; ++fw) {
+        const Word3 f = load_word<L>(pv.ref, fb, fw, W);
+        ReadWin r;
+        r.lo0 = __funnelshift_rc(ra.lo, rb0.lo, rs);
+        r.hi0 = __funnelshift_rc(ra.hi, rb0.hi, rs);
+        r.nm0 = __funnelshift_rc(ra.nm, rb0.nm, rs);
+        r.lo1 = __funnelshift_rc(rb0.lo, rc.lo, rs);
+        r.hi1 = __funnelshift_rc(rb0.hi, rc.hi, rs);
+        r.nm1 = __funnelshift_rc(rb0.nm, rc.nm, rs);
+        if constexpr (sizeof(U) == 8) {
+            r.lo2 = __funnelshift_rc(rc.lo, rd.lo, rs);
+            r.hi2 = __funnelshift_rc(rc.hi, rd.hi, rs);
+            r.nm2 = __funnelshift_rc(rc.nm, rd.nm, rs);
+        } else {
+            r.lo2 = r.hi2 = r.nm2 = 0u;
         }
-        const unsigned sh = (unsigned)s & 31u;
-        const U wlo = window<U>(r0.lo, r1.lo, r2.lo, sh);
-        const U whi = window<U>(r0.hi, r1.hi, r2.hi, sh);
-        const U wnm = window<U>(r0.nm, r1.nm, r2.nm, sh);
-        // reference base F[j-1]
-        const int fbit = (j - 1) & 31;
-        if (fbit == 0 && j > 1) f = load_word<L>(pv.ref, fb, (j - 1) >> 5, W);
-        const U mlo = U(0) - U((f.lo >> fbit) & 1u);
-        const U mhi = U(0) - U((f.hi >> fbit) & 1u);
-        const U fn = U(0) - U((f.nm >> fbit) & 1u);
-        // Eq bit q: read[j-E-1+q] equals F[j-1], neither N; bit 0 is the
-        // row j-E, whose read base is read[j-E-1] = bit 0 of the window.
-        const U Eq = ~((wlo ^ mlo) | (whi ^ mhi) | wnm | fn) & band_mask;
-
-        const U Pv = VP | bottom;
-        const U Mv = VN;
-        const U X = Eq | Mv;
-        const U D0 = (((X & Pv) + Pv) ^ Pv) | X;
-        U Ph = Mv | ~(D0 | Pv);
-        U Mh = Pv & D0;
-        Ph = (Ph << 1) | U(1);   // +1 enters above the top row
-        Mh = Mh << 1;
-        const U nPv = Mh | ~(D0 | Ph);
-        const U nMv = Ph & D0;
-        T += 1 + (int)(nPv & U(1)) - (int)(nMv & U(1));
-        VP = (nPv >> 1) & store_mask;
-        VN = (nMv >> 1) & store_mask;
+        const int ncol = min(32, m - 32 * fw);
+        uint32_t accP = 0u, accM = 0u;
+        if (ncol == 32) {
+#pragma unroll
+            for (int t = 0; t < 32; ++t)
+                column<U>(r, f, t, store_mask, bottom, VP, VN, accP, accM);
+        } else {
+            for (int t = 0; t < ncol; ++t)
+                column<U>(r, f, t, store_mask, bottom, VP, VN, accP, accM);
+        }
+        // top cell D(j-E, j) after the word: each column adds 1 + its top
+        // row's new difference
+        T += ncol + __popc(accP) - __popc(accM);
+        // Early exit: the band's smallest value is at least T minus the
+        // number of -1 differences.  Past E, every path through this column
+        // costs more than E, so the distance saturates (the values that the
+        // band computes are exact wherever they are <= E).
+        if (T - Bits<U>::popc(VN) > E) return E + 1;
+        ra = rb0;
+        rb0 = rc;
+        if constexpr (sizeof(U) == 8) {
+            rc = rd;
+            rd = load_word<L>(pv.read, rb, fw + 3, W);
+        } else {
+            rc = load_word<L>(pv.read, rb, fw + 2, W);
+        }
     }
     const U first = (U(1) << E) - 1;
     const int dist = T + Bits<U>::popc(VP & first) - Bits<U>::popc(VN & first);

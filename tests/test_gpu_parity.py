@@ -141,6 +141,42 @@ def test_pack_invalid_bytes_report_and_pack_as_n(pf, ctx):
     assert np.array_equal(out.lo.cpu().numpy()[:total].view(np.uint32), lo)
 
 
+def test_pack_neighbour_bytes_never_leak(pf, ctx):
+    """Bytes past a sequence's end (the next sequence's, or whatever follows
+    the buffer) never change its planes, and raise the error only when they
+    belong to a sequence that holds them."""
+    from gpu_util import to_dev
+    rng = np.random.default_rng(9)
+    acgt = np.frombuffer(b"ACGT", np.uint8)
+    # ragged: a valid 40-byte sequence followed by one that starts with bad bytes
+    seqs = [rng.choice(acgt, 40), np.frombuffer(b"XY#" + b"C" * 37, np.uint8),
+            rng.choice(acgt, 33)]
+    src = np.concatenate(seqs)
+    off = np.array([0, 40, 80, 113], dtype=np.int64)
+    wo, total = pf.pf_pack_layout(off)
+    out = pf.Seqs.empty(total, "cuda:0", word_off=to_dev(wo))
+    pf.pf_pack(ctx, to_dev(src), to_dev(off), to_dev(wo), out)
+    with pytest.raises(pf.PFError):
+        pf.pf_sync(ctx)
+    _, lo, hi, nm, bad = oracle.pack_batch(src, off)
+    assert bad == 3
+    for got, want in ((out.lo, lo), (out.hi, hi), (out.nmask, nm)):
+        assert np.array_equal(got.cpu().numpy()[:total].view(np.uint32), want)
+    # fixed: the buffer is a slice followed by bytes that are not bases
+    for length in (37, 150, 250):
+        n = 64
+        whole = np.concatenate([rng.choice(acgt, n * length), np.frombuffer(b"#" * 64, np.uint8)])
+        dev = to_dev(whole)
+        W = (length + 31) // 32
+        out = pf.Seqs.empty(n * W, "cuda:0", stride_words=W)
+        pf.pf_pack_fixed(ctx, dev[:n * length], n, length, out)
+        pf.pf_sync(ctx)  # no error: the '#' bytes are outside every sequence
+        _, lo, hi, nm, _ = oracle.pack_batch(whole[:n * length],
+                                             np.arange(n + 1, dtype=np.int64) * length)
+        for got, want in ((out.lo, lo), (out.hi, hi), (out.nmask, nm)):
+            assert np.array_equal(got.cpu().numpy().view(np.uint32), want)
+
+
 # ---- a2-a4 filter ---------------------------------------------------------
 
 CASES = [
