@@ -73,6 +73,11 @@ __device__ __forceinline__ uint32_t shr_pair(uint32_t a, uint32_t b, int d) {
 
 __device__ __forceinline__ int imin(int a, int b) { return a < b ? a : b; }
 
+// -1, read from memory so that the compiler cannot fold it: the SneakySnake
+// step negates as y * (-1), which runs on the multiply-add pipe and leaves
+// the integer ALU pipe (the filter's binding unit) to the logic operations.
+static __device__ uint32_t g_minus_one = 0xffffffffu;
+
 // The resumable state of one pair.  init() loads the first words, word()
 // processes one reference word and reports whether both deciders are
 // decided, finish() closes GateKeeper's last word.  Every lane of the
@@ -90,12 +95,19 @@ struct PairFilter {
     // one bit per slot
     using Mask = typename std::conditional<(NS > 32), unsigned long long, uint32_t>::type;
 
-    uint32_t Mp[NS], Mpp[NS];  // GateKeeper: mask words of words w-1 and w-2
+    // Mask words of three consecutive words.  Word w's masks go into the
+    // array that held word w-3's; the other two are GateKeeper's words w-1
+    // and w-2.  The word loop is unrolled three times so that the roles
+    // rotate by name instead of by copying (role r: w-1 in P[r], w-2 in
+    // P[r+2 mod 3], new word into P[r+1 mod 3]).
+    uint32_t P0[NS], P1[NS], P2[NS];
+    int role;
     Mask dead;            // SneakySnake: slots blocked before the current word
     uint32_t C;           // SneakySnake: columns >= checkpoint in this word
     int kss;
     bool ss_done, gk_done, cont;
     int h, fc;
+    uint32_t neg1;        // -1 (see g_minus_one)
 
     __device__ __forceinline__ bool live(int k, int g) const {
         if constexpr (XE >= 0) return true;
@@ -121,7 +133,8 @@ struct PairFilter {
         Rp1 = load_word<L>(pv.read, rb, 1, W);
         Fw = load_word<L>(pv.ref, fb, 0, W);
 #pragma unroll
-        for (int k = 0; k < NS; ++k) { Mp[k] = 0u; Mpp[k] = 0u; }
+        for (int k = 0; k < NS; ++k) { P0[k] = 0u; P2[k] = 0u; }
+        role = 0;
         dead = 0u;
         C = 0xffffffffu;
         kss = 0;
@@ -130,15 +143,34 @@ struct PairFilter {
         gk_done = !GK;
         h = 0;
         fc = 0;
+        neg1 = *(volatile const uint32_t *)&g_minus_one;
     }
 
     __device__ __forceinline__ bool done() const { return (ss_done && gk_done) || w >= W; }
 
-    // Process reference word w; returns done().
-    __device__ __forceinline__ bool word(const PairsView &pv, int g, unsigned gmask) {
+    // Process every remaining word, then leave `role` for finish().
+    __device__ __forceinline__ void run(const PairsView &pv, int g, unsigned gmask) {
+        if constexpr (!GK) {  // no history to rotate
+            while (!done()) word(pv, g, gmask, P0, P2, P1);
+            return;
+        }
+        for (;;) {
+            if (done()) { role = 0; return; }
+            word(pv, g, gmask, P0, P2, P1);
+            if (done()) { role = 1; return; }
+            word(pv, g, gmask, P1, P0, P2);
+            if (done()) { role = 2; return; }
+            word(pv, g, gmask, P2, P1, P0);
+        }
+    }
+
+    // Process reference word w with GateKeeper's words w-1 (Mp) and w-2
+    // (Mpp); word w's mask words are written to M.
+    __device__ __forceinline__ void word(const PairsView &pv, int g, unsigned gmask,
+                                         const uint32_t (&Mp)[NS], const uint32_t (&Mpp)[NS],
+                                         uint32_t (&M)[NS]) {
         const Word3 F = Fw;
         Fw = load_word<L>(pv.ref, fb, w + 1, W);  // prefetch the next reference word
-        uint32_t M[NS];
 
         // ---- map words of this lane's diagonals
         Word3 A, B;
@@ -187,7 +219,7 @@ struct PairFilter {
                     for (int k = 0; k < NS; ++k) {
                         if (!live(k, g)) continue;
                         const uint32_t y = M[k] | (uint32_t)((dead >> k) & 1u);
-                        T &= (y | (0u - y));
+                        T &= (y | (y * neg1));
                     }
                     T = group_and<TPP>(T, gmask);
                     if (T == 0u) {
@@ -220,7 +252,7 @@ struct PairFilter {
                     for (int k = 0; k < NS; ++k) {
                         if (!live(k, g)) continue;
                         const uint32_t y = M[k] & C;
-                        T &= (y | (0u - y));
+                        T &= (y | (y * neg1));
                     }
                     T = group_and<TPP>(T, gmask);
                     if (T == 0u) {
@@ -274,12 +306,6 @@ struct PairFilter {
                     fc += __popc(Fa);  // word w-1 is full: every bit is a column < m
                     if (h > thr() && fc > thr()) gk_done = true;
                 }
-#pragma unroll
-                for (int k = 0; k < NS; ++k) {
-                    if (!live(k, g)) continue;
-                    Mpp[k] = Mp[k];
-                    Mp[k] = M[k];
-                }
             }
         }
 
@@ -287,11 +313,18 @@ struct PairFilter {
         R0 = Rp1;
         Rp1 = load_word<L>(pv.read, rb, w + 2, W);
         ++w;
-        return done();
     }
 
     // Counts once done(): SneakySnake's obstacles and GateKeeper's edits.
     __device__ __forceinline__ void finish(int g, unsigned gmask, int *ss_count, int *gk_count) {
+        if (role == 0) finish_words(g, gmask, P0, P2, ss_count, gk_count);
+        else if (role == 1) finish_words(g, gmask, P1, P0, ss_count, gk_count);
+        else finish_words(g, gmask, P2, P1, ss_count, gk_count);
+    }
+
+    __device__ __forceinline__ void finish_words(int g, unsigned gmask, const uint32_t (&Mp)[NS],
+                                                 const uint32_t (&Mpp)[NS], int *ss_count,
+                                                 int *gk_count) {
         const int E = thr();
         if constexpr (SS) *ss_count = imin(kss, E + 1);
         if constexpr (GK) {
@@ -369,7 +402,7 @@ __device__ __forceinline__ void filter_group(const FilterArgs &a, int64_t p, int
     if (!pair_args<TPP, DPT, DEC, XE>(a, p, g, &m, &E)) return;
     PairFilter<TPP, DPT, DEC, XE> st;
     st.init(a.pairs, p, m, E);
-    while (!st.done()) st.word(a.pairs, g, gmask);
+    st.run(a.pairs, g, gmask);
     int ssc = 0, gkc = 0;
     st.finish(g, gmask, &ssc, &gkc);
     if (g == 0) write_outputs<DEC>(a, p, E, ssc, gkc);

@@ -141,7 +141,7 @@ __device__ __forceinline__ void serve_filter_chunk(const ServeDesc &d, const Pai
         }
         PairFilter<kServeTpp, kServeDpt, DEC, -1, LdCG> st;
         st.init(pv, p, m, E);
-        while (!st.done()) st.word(pv, g, gmask);
+        st.run(pv, g, gmask);
         int ssc = 0, gkc = 0;
         st.finish(g, gmask, &ssc, &gkc);
         if (g == 0) write_outputs<DEC>(a, p, E, ssc, gkc);
