@@ -79,41 +79,24 @@ bin_scatter_kernel(const int16_t *E, int64_t n, int E_max, BinTable t,
     __shared__ unsigned cnt[kNumBatchCfgs];
     __shared__ unsigned long long base[kNumBatchCfgs];
     if (*ident) return;
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    for (int i = threadIdx.x; i < kNumBatchCfgs; i += blockDim.x) cnt[i] = 0;
-    __syncthreads();
-    int key = -1;
-    unsigned rank = 0;
-    if (p < n) {
-        key = bin_key(E, p, E_max, t);
-        rank = atomicAdd(&cnt[key], 1u);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < kNumBatchCfgs; i += blockDim.x)
-        base[i] = cnt[i] ? atomicAdd(&cursor[i], (unsigned long long)cnt[i]) : 0ull;
-    __syncthreads();
-    if (p < n) order[base[key] + rank] = p;
-}
-
-// dist[p] = E_p + 1 for pairs the filter rejected (verification skips them)
-__global__ void __launch_bounds__(256)
-dist_fill_rejected_kernel(const uint8_t *accept, const int16_t *E, int E_max, int64_t n,
-                          int32_t *dist) {
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        if (!accept[p]) {
-            const int e = E ? (int)E[p] : E_max;
-            dist[p] = (e < 0 || e > E_max) ? -1 : e + 1;
+    for (int64_t p0 = (int64_t)blockIdx.x * blockDim.x; p0 < n;
+         p0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = p0 + threadIdx.x;
+        for (int i = threadIdx.x; i < kNumBatchCfgs; i += blockDim.x) cnt[i] = 0;
+        __syncthreads();
+        int key = -1;
+        unsigned rank = 0;
+        if (p < n) {
+            key = bin_key(E, p, E_max, t);
+            rank = atomicAdd(&cnt[key], 1u);
         }
+        __syncthreads();
+        for (int i = threadIdx.x; i < kNumBatchCfgs; i += blockDim.x)
+            base[i] = cnt[i] ? atomicAdd(&cursor[i], (unsigned long long)cnt[i]) : 0ull;
+        __syncthreads();
+        if (p < n) order[base[key] + rank] = p;
+        __syncthreads();  // cnt and base are reused by the next tile
     }
-}
-
-cudaError_t launch_dist_fill(const uint8_t *accept, const int16_t *E, int E_max, int64_t n,
-                             int32_t *dist, int sms, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    const int64_t fb = std::min<int64_t>((n + 255) / 256, (int64_t)sms * 16);
-    dist_fill_rejected_kernel<<<(unsigned)fb, 256, 0, st>>>(accept, E, E_max, n, dist);
-    return cudaGetLastError();
 }
 
 }  // namespace pf
@@ -303,7 +286,7 @@ pf_status pf_ctx::run_batched(unsigned dec, const FilterArgs &a, const Scratch &
         bin_hist_kernel<<<(unsigned)std::max<int64_t>(hb, 1), 256, 0, stream>>>(a.E, a.n, a.E_max,
                                                                                t, s.hist);
         bin_scan_kernel<<<1, 32, 0, stream>>>(s.hist, s.bin_start, s.cursor, s.ident);
-        bin_scatter_kernel<<<(unsigned)((a.n + 255) / 256), 256, 0, stream>>>(
+        bin_scatter_kernel<<<(unsigned)std::max<int64_t>(hb, 1), 256, 0, stream>>>(
             a.E, a.n, a.E_max, t, s.cursor, s.order, s.ident);
     }
     pf_status st = cuda(cudaGetLastError(), "binning launch");
@@ -549,15 +532,13 @@ pf_status pf_filter_verify(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs
     Scratch s;
     st = ctx->scratch_layout(n, &s);
     if (st != PF_OK) return st;
-    const FilterArgs a = make_filter_args(ctx, pairs, lens, E, E_max, accept, count, n);
+    FilterArgs a = make_filter_args(ctx, pairs, lens, E, E_max, accept, count, n);
+    a.dist = dist;  // the filter writes E + 1 for the pairs it rejects
     st = ctx->run_batched(deciders, a, s);
     if (st != PF_OK) return st;
     // the first selected decider's accept flags choose the pairs to verify
     st = ctx->cuda(launch_compact(accept, n, s.idx, s.n_idx, s.tiles, ctx->stream),
                    "compact launch");
-    if (st != PF_OK) return st;
-    st = ctx->cuda(launch_dist_fill(accept, E, E_max, n, dist, ctx->sms, ctx->stream),
-                   "fill launch");
     if (st != PF_OK) return st;
     return ctx->cuda(launch_verify(to_view(pairs), lens, E, E_max, s.idx, s.n_idx, n, dist,
                                    ctx->d_err, ctx->sms, ctx->stream),

@@ -356,6 +356,7 @@ struct PairFilter {
 template <int DEC>
 __device__ __forceinline__ void write_outputs(const FilterArgs &a, int64_t p, int E, int ssc,
                                               int gkc) {
+    if (a.dist && (DEC == 2 ? gkc : ssc) > E) a.dist[p] = E + 1;  // not verified
     if constexpr (DEC == 3) {
         a.count[p] = (int16_t)ssc;
         a.accept[p] = (uint8_t)(ssc <= E);
@@ -374,6 +375,7 @@ template <int DEC>
 __device__ __forceinline__ void write_invalid(const FilterArgs &a, int64_t p) {
     a.count[p] = -1;
     a.accept[p] = 0;
+    if (a.dist) a.dist[p] = -1;
     if constexpr (DEC == 3) {
         a.count[a.n + p] = -1;
         a.accept[a.n + p] = 0;

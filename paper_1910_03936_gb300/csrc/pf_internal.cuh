@@ -78,13 +78,14 @@ __device__ __forceinline__ uint32_t group_and(uint32_t x, unsigned gmask) {
 // Filter launch parameters shared by the plain and the batched kernels.
 struct FilterArgs {
     PairsView pairs;
-    const int32_t *lens;
-    const int16_t *E;     // null: every pair uses E_max
-    int E_max;
-    uint8_t *accept;
-    int16_t *count;
-    int64_t n;
-    unsigned *err;
+    const int32_t *lens = nullptr;
+    const int16_t *E = nullptr;     // null: every pair uses E_max
+    int E_max = 0;
+    uint8_t *accept = nullptr;
+    int16_t *count = nullptr;
+    int64_t n = 0;
+    unsigned *err = nullptr;
+    int32_t *dist = nullptr;  // non-null: E + 1 for pairs the first decider rejects, -1 if invalid
 };
 
 // Batched (scheduler) launch: pairs taken in chunks from `order` (null:

@@ -53,8 +53,6 @@ cudaError_t launch_pack_fixed(const uint8_t *ascii, int64_t nseq, int len, uint3
 int64_t compact_tiles(int64_t n);
 cudaError_t launch_compact(const uint8_t *flags, int64_t n, int64_t *idx, int64_t *n_out,
                            int64_t *tile_scratch, cudaStream_t st);
-cudaError_t launch_dist_fill(const uint8_t *accept, const int16_t *E, int E_max, int64_t n,
-                             int32_t *dist, int sms, cudaStream_t st);
 cudaError_t launch_verify(const PairsView &pv, const int32_t *lens, const int16_t *E, int E_max,
                           const int64_t *idx, const int64_t *n_idx, int64_t n, int32_t *dist,
                           unsigned *err, int sms, cudaStream_t st);

@@ -170,13 +170,13 @@ pf_status enqueue_chunk(Job &J, Slot &s, int64_t nc) {
     a.count = s.cnt;
     a.n = nc;
     a.err = ctx->d_err;
+    a.dist = s.dist;  // E + 1 for the pairs the filter rejects
     cudaStream_t saved = ctx->stream;
     ctx->stream = s.st;
     pf_status st = ctx->run_batched(J.dec, a, s.scr);
     ctx->stream = saved;
     if (st != PF_OK) return st;
     e = launch_compact(s.acc, nc, s.scr.idx, s.scr.n_idx, s.scr.tiles, s.st);
-    if (e == cudaSuccess) e = launch_dist_fill(s.acc, a.E, J.E_max, nc, s.dist, ctx->sms, s.st);
     if (e == cudaSuccess)
         e = launch_verify(pv, s.lens, a.E, J.E_max, s.scr.idx, s.scr.n_idx, nc, s.dist,
                           ctx->d_err, ctx->sms, s.st);

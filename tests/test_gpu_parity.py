@@ -297,6 +297,17 @@ def test_invalid_per_pair_threshold(pf, ctx):
             filter_dev(ctx, D, 3, plain=plain)
         assert ei.value.status == 1
         pf.pf_sync(ctx)
+    # the whole path marks the invalid pair (count -1, dist -1) and no other
+    n = D.n
+    acc = torch.zeros(2 * n, dtype=torch.uint8, device="cuda:0")
+    cnt = torch.zeros(2 * n, dtype=torch.int16, device="cuda:0")
+    dist = torch.full((n,), -5, dtype=torch.int32, device="cuda:0")
+    pf.pf_filter_verify(ctx, 3, D.pairs, D.lens, D.E, D.E_max, acc, cnt, dist, n)
+    with pytest.raises(pf.PFError):
+        pf.pf_sync(ctx)
+    pf.pf_sync(ctx)
+    assert dist.cpu().tolist() == [0, -1, 0]
+    assert cnt.cpu().tolist() == [0, -1, 0, 0, -1, 0]
 
 
 def test_host_checks_reject_bad_arguments(pf, ctx, case_data):
