@@ -65,7 +65,12 @@ def _load():
         lib.or_pack.restype = i32
         lib.or_filter_batch.argtypes = [p, p, p, p, p, p, i32, u32, p, p, i64, i32]
         lib.or_filter_batch.restype = None
-        lib.or_int_batch.argtypes = [i32, p, p, p, p, p, p, i32, p, i64, i32]
+        lib.or_int_batch.argtypes = [i32, p, p, p, p, p, p, i32, p, i64, i32, i32, i32]
+        lib.or_sneakysnake_partitioned.argtypes = [ctypes.c_char_p, ctypes.c_char_p, i32, i32,
+                                                   i32, i32]
+        lib.or_shouji.argtypes = [ctypes.c_char_p, ctypes.c_char_p, i32, i32]
+        lib.or_shouji_vector.argtypes = [ctypes.c_char_p, ctypes.c_char_p, i32, i32, p]
+        lib.or_gatekeeper_shd.argtypes = [ctypes.c_char_p, ctypes.c_char_p, i32, i32, i32, i32]
         lib.or_int_batch.restype = None
         lib.or_pack_batch.argtypes = [p, p, i64, p, p, p, p]
         lib.or_pack_batch.restype = i64
@@ -98,6 +103,36 @@ def sneakysnake_full(R, F, E):
 def sneakysnake_dp(R, F, E):
     R, F = _b(R), _b(F)
     return _load().or_sneakysnake_dp(R, F, len(R), E)
+
+
+def sneakysnake_partitioned(R, F, E, t, y):
+    """Partitioned SneakySnake (sub-matrices of t columns, y replications
+    each), min(count, E+1)."""
+    R, F = _b(R), _b(F)
+    assert len(R) == len(F) and t >= 1 and y >= 1
+    return _load().or_sneakysnake_partitioned(R, F, len(R), E, t, y)
+
+
+def shouji(R, F, E):
+    """Shouji count min(ones of the Shouji bit-vector, E+1)."""
+    R, F = _b(R), _b(F)
+    assert len(R) == len(F)
+    return _load().or_shouji(R, F, len(R), E)
+
+
+def shouji_vector(R, F, E):
+    """The Shouji bit-vector (uint8[m]) and its number of ones."""
+    R, F = _b(R), _b(F)
+    v = np.zeros(max(len(R), 1), dtype=np.uint8)
+    ones = _load().or_shouji_vector(R, F, len(R), E, _ptr(v))
+    return v[:len(R)], ones
+
+
+def gatekeeper_shd(R, F, E, vacant_zero=True, streak=True):
+    """GateKeeper with SHD's vacant-zero masks and/or streak counting."""
+    R, F = _b(R), _b(F)
+    assert len(R) == len(F)
+    return _load().or_gatekeeper_shd(R, F, len(R), E, int(vacant_zero), int(streak))
 
 
 def sneakysnake_trace(R, F, E):
@@ -182,19 +217,21 @@ def filter_batch(pairs, deciders=SNEAKYSNAKE | GATEKEEPER, E=None, threads=None)
     return acc, cnt
 
 
-_KINDS = {"wf_banded": 1, "wf": 2, "ss_dp": 3, "ss_full": 4, "hamming": 5}
+_KINDS = {"wf_banded": 1, "wf": 2, "ss_dp": 3, "ss_full": 4, "hamming": 5,
+          "ss_partitioned": 6, "shouji": 7, "gk_shd": 8}
 
 
-def int_batch(kind, pairs, E=None, threads=None):
+def int_batch(kind, pairs, E=None, threads=None, p0=0, p1=0):
     """Per-pair integers: 'wf_banded' (min(ED, E+1)), 'wf', 'ss_dp',
-    'ss_full', 'hamming'."""
+    'ss_full', 'hamming', 'ss_partitioned' (p0 = t, p1 = y), 'shouji',
+    'gk_shd' (p0 = vacant zero, p1 = streak counting)."""
     lib = _load()
     n = pairs.n
     e, stride = _E_arr(pairs.E if E is None else E)
     out = np.zeros(n, dtype=np.int32)
     lib.or_int_batch(_KINDS[kind], _ptr(pairs.reads), _ptr(pairs.read_off), _ptr(pairs.refs),
                      _ptr(pairs.ref_off), _ptr(np.ascontiguousarray(pairs.lens, np.int32)),
-                     _ptr(e), stride, _ptr(out), n, _threads(threads))
+                     _ptr(e), stride, _ptr(out), n, _threads(threads), int(p0), int(p1))
     return out
 
 

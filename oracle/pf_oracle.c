@@ -42,6 +42,29 @@
  *   R9  base codes A=00, C=01, G=10, T=11 (only A=00 and T=11 are printed
  *       in §5.2.3); N packs as code 00 with its N bit set; bases past the
  *       end of a sequence in its last 32-bit word pack as N.
+ *   R15 partitioned SneakySnake (§8.5): sub-matrix s covers columns
+ *       [s*t, min((s+1)*t, m)); its pipes end at its own last column (a
+ *       pipe that reaches it leaves the sub-matrix, no obstacle), so the
+ *       last, narrower sub-matrix holds only real columns; it contributes
+ *       min(y, t_s - sum of the y pipe depths), which equals the obstacles
+ *       its y replications pass.  The total saturates at E+1 like R5.
+ *   R16 Shouji (Ch. 6): window c covers columns c..c+3 for every c in
+ *       [0, m); window cells past column m-1 read as 1 and the bit-vector
+ *       has no bits there; the bit-vector starts all 1; a diagonal's 4-bit
+ *       vector wins with more zeros, on a tie the first one (in row order
+ *       d = -E .. E) whose first bit is 0, else the first one; it replaces
+ *       the bit-vector's bits c..c+3 only with strictly more zeros than
+ *       they hold.  The count saturates at E+1 like R5.  Parity partly
+ *       unpinned: the 4-column window, the example of Fig. 6.1 and zero
+ *       false rejects are pinned, but the tie order, the strict
+ *       replacement and the value of window cells past the end are
+ *       readings that change the count of some pairs and that no printed
+ *       example fixes.
+ *   R17 SHD-style GateKeeper (Ch. 3): "vacant zero" fills the out-of-range
+ *       cells of the masks with 0 (SHD's arithmetic shifts) instead of R2's
+ *       1; the "streak" counter charges each maximal run of L ones in the
+ *       final bit-vector ceil(L/3) edits, the counting that charges three
+ *       consecutive ones as a single edit (Ch. 3, Conservative Counting).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -309,6 +332,145 @@ int or_gatekeeper(const uint8_t *R, const uint8_t *F, int m, int E)
 }
 
 /* ------------------------------------------------------------------ */
+/* SneakySnake on sub-matrices of t columns (§8.5, R15)                */
+/* ------------------------------------------------------------------ */
+
+/* Obstacles that y replications of the search pass in the sub-matrix
+ * [b, b+ts) of the map: each replication finds the largest number of
+ * leading zeros x over the 2E+1 rows from the current column (a run stops
+ * at the sub-matrix's last column: reaching it leaves the sub-matrix
+ * without an obstacle), then every row shifts by x+1.  Returns
+ * min(y, ts - sum x). */
+static int or_submatrix_obstacles(const uint8_t *map, int m, int E, int b, int ts, int y)
+{
+    int c = 0, sum_x = 0;
+    for (int o = 0; o < y; ++o) {
+        int x = 0;
+        for (int d = -E; d <= E; ++d) {
+            int r = 0;
+            while (c + r < ts && map[(size_t)(d + E) * m + b + c + r] == 0) r++;
+            if (r > x) x = r;
+        }
+        sum_x += x;
+        c += x + 1;
+        if (c > ts) c = ts;  /* past the end every row reads as leading ones */
+    }
+    int k = ts - sum_x;
+    return k < y ? k : y;
+}
+
+/* Partitioned SneakySnake count min(sum over sub-matrices, E+1). */
+int or_sneakysnake_partitioned(const uint8_t *R, const uint8_t *F, int m, int E, int t, int y)
+{
+    if (m <= 0) return 0;
+    uint8_t *map = (uint8_t *)malloc((size_t)(2 * E + 1) * m);
+    or_neighborhood_map(R, F, m, E, map);
+    int total = 0;
+    for (int b = 0; b < m; b += t) {
+        int ts = (m - b < t) ? m - b : t;
+        total += or_submatrix_obstacles(map, m, E, b, ts, y);
+    }
+    free(map);
+    return total > E + 1 ? E + 1 : total;
+}
+
+/* ------------------------------------------------------------------ */
+/* Shouji (Ch. 6, R16)                                                 */
+/* ------------------------------------------------------------------ */
+
+/* Runs Methods 1-2 of Ch. 6 and leaves the Shouji bit-vector in sbv[m];
+ * returns its number of ones (unsaturated). */
+int or_shouji_vector(const uint8_t *R, const uint8_t *F, int m, int E, uint8_t *sbv)
+{
+    if (m <= 0) return 0;
+    uint8_t *map = (uint8_t *)malloc((size_t)(2 * E + 1) * m);
+    or_neighborhood_map(R, F, m, E, map);
+    for (int i = 0; i < m; ++i) sbv[i] = 1;
+    for (int c = 0; c < m; ++c) {
+        /* Step 1: the 4-bit diagonal vector of window c with the most zeros */
+        int best = 0, best_z = -1, best_lead = 0;
+        for (int d = -E; d <= E; ++d) {
+            int z = 0;
+            for (int q = 0; q < 4; ++q) {
+                int col = c + q;
+                int bit = (col < m) ? map[(size_t)(d + E) * m + col] : 1;
+                z += bit ? 0 : 1;
+            }
+            int lead = map[(size_t)(d + E) * m + c] == 0;
+            if (z > best_z || (z == best_z && lead && !best_lead)) {
+                best = d;
+                best_z = z;
+                best_lead = lead;
+            }
+        }
+        /* Step 2: keep it if it has more zeros than the bit-vector there */
+        int cur_z = 0;
+        for (int q = 0; q < 4 && c + q < m; ++q) cur_z += sbv[c + q] ? 0 : 1;
+        if (best_z > cur_z)
+            for (int q = 0; q < 4 && c + q < m; ++q)
+                sbv[c + q] = map[(size_t)(best + E) * m + c + q];
+    }
+    free(map);
+    /* Method 3: the edits are the ones of the bit-vector */
+    int ones = 0;
+    for (int i = 0; i < m; ++i) ones += sbv[i];
+    return ones;
+}
+
+/* Shouji count min(ones of the bit-vector, E+1). */
+int or_shouji(const uint8_t *R, const uint8_t *F, int m, int E)
+{
+    if (m <= 0) return 0;
+    uint8_t *sbv = (uint8_t *)malloc((size_t)m);
+    int ones = or_shouji_vector(R, F, m, E, sbv);
+    free(sbv);
+    return ones > E + 1 ? E + 1 : ones;
+}
+
+/* ------------------------------------------------------------------ */
+/* GateKeeper with SHD's conventions (Ch. 3, R17)                      */
+/* ------------------------------------------------------------------ */
+
+/* GateKeeper with two switches: vacant_zero fills out-of-range mask cells
+ * with 0 instead of 1, streak charges each run of L ones ceil(L/3) edits
+ * instead of L.  Both off: or_gatekeeper.  Returns min(count, E+1). */
+int or_gatekeeper_shd(const uint8_t *R, const uint8_t *F, int m, int E, int vacant_zero,
+                      int streak)
+{
+    if (m <= 0) return 0;
+    int h = or_hamming(R, F, m);
+    if (h <= E) return h;
+    uint8_t *map = (uint8_t *)malloc((size_t)(2 * E + 1) * m);
+    uint8_t *amended = (uint8_t *)malloc((size_t)m);
+    uint8_t *final_mask = (uint8_t *)malloc((size_t)m);
+    or_neighborhood_map(R, F, m, E, map);
+    if (vacant_zero)
+        for (int d = -E; d <= E; ++d)
+            for (int i = 0; i < m; ++i)
+                if (i + d < 0 || i + d >= m) map[(size_t)(d + E) * m + i] = 0;
+    for (int i = 0; i < m; ++i) final_mask[i] = 1;
+    for (int d = -E; d <= E; ++d) {
+        or_amend(map + (size_t)(d + E) * m, m, amended);
+        for (int i = 0; i < m; ++i) final_mask[i] = final_mask[i] & amended[i];
+    }
+    int count = 0;
+    if (streak) {
+        int run = 0;
+        for (int i = 0; i <= m; ++i) {
+            if (i < m && final_mask[i]) { run++; continue; }
+            count += (run + 2) / 3;
+            run = 0;
+        }
+    } else {
+        for (int i = 0; i < m; ++i) count += final_mask[i];
+    }
+    free(final_mask);
+    free(amended);
+    free(map);
+    return count > E + 1 ? E + 1 : count;
+}
+
+/* ------------------------------------------------------------------ */
 /* Edit distance (Ch. 2 "Accelerating Read Alignment"; Ch. 3 metrics)  */
 /* ------------------------------------------------------------------ */
 
@@ -379,7 +541,10 @@ typedef struct {
     int16_t *count;
     int32_t *dist;
     int64_t n, begin, end;
-    int kind; /* 0 filter, 1 verify, 2 full WF, 3 SS dp, 4 SS full, 5 hamming */
+    int kind; /* 0 filter, 1 verify, 2 full WF, 3 SS dp, 4 SS full, 5 hamming,
+                 6 partitioned SS (p0 = t, p1 = y), 7 Shouji,
+                 8 SHD-style GateKeeper (p0 = vacant zero, p1 = streak) */
+    int p0, p1;
 } or_job;
 
 static void *or_run_job(void *arg)
@@ -411,6 +576,9 @@ static void *or_run_job(void *arg)
         case 3: j->dist[p] = or_sneakysnake_dp(R, F, m, E); break;
         case 4: j->dist[p] = or_sneakysnake_full(R, F, m, E); break;
         case 5: j->dist[p] = or_hamming(R, F, m); break;
+        case 6: j->dist[p] = or_sneakysnake_partitioned(R, F, m, E, j->p0, j->p1); break;
+        case 7: j->dist[p] = or_shouji(R, F, m, E); break;
+        case 8: j->dist[p] = or_gatekeeper_shd(R, F, m, E, j->p0, j->p1); break;
         }
     }
     return NULL;
@@ -454,17 +622,19 @@ void or_filter_batch(const uint8_t *reads, const int64_t *read_off,
 }
 
 /* Per-pair integer results: kind 1 banded WF min(ED, E+1), 2 full WF,
- * 3 SneakySnake DP formulation, 4 unsaturated SneakySnake, 5 Hamming. */
+ * 3 SneakySnake DP formulation, 4 unsaturated SneakySnake, 5 Hamming,
+ * 6 partitioned SneakySnake (p0 = t, p1 = y), 7 Shouji, 8 SHD-style
+ * GateKeeper (p0 = vacant zero, p1 = streak counting). */
 void or_int_batch(int kind, const uint8_t *reads, const int64_t *read_off,
                   const uint8_t *refs, const int64_t *ref_off,
                   const int32_t *lens, const int16_t *E, int E_stride,
-                  int32_t *out, int64_t n, int nthreads)
+                  int32_t *out, int64_t n, int nthreads, int p0, int p1)
 {
     or_job j;
     memset(&j, 0, sizeof j);
     j.reads = reads; j.refs = refs; j.read_off = read_off; j.ref_off = ref_off;
     j.lens = lens; j.E = E; j.E_stride = E_stride;
-    j.dist = out; j.n = n; j.kind = kind;
+    j.dist = out; j.n = n; j.kind = kind; j.p0 = p0; j.p1 = p1;
     or_run(j, nthreads);
 }
 

@@ -335,3 +335,134 @@ def test_zero_false_rejects_on_synthetic_reads(m, E, kind):
     assert np.all(cnt[0] <= np.minimum(wf, E + 1))
     assert np.array_equal(oracle.verify_batch(P), np.minimum(wf, E + 1))
     assert np.array_equal(cnt[0], oracle.int_batch("ss_dp", P))
+
+
+# ---- NEXT rows: partitioned SneakySnake (§8.5), Shouji (Ch. 6), SHD-style
+# GateKeeper (Ch. 3) -------------------------------------------------------
+
+def test_partitioned_lzc_example():
+    kv, _ = read_golden("lzc_example.txt")
+    row = kv["row_msb_first"][::-1]          # column 0 first
+    t, y = int(kv["t"]), int(kv["y"])
+    ref = "".join("A" for _ in row)
+    read = "".join("C" if b == "1" else "A" for b in row)
+    assert oracle.sneakysnake_partitioned(read, ref, 0, t, y) == int(kv["obstacles"])
+    xs = [int(v) for v in kv["x"].split(",")]
+    assert int(kv["obstacles"]) == min(y, t - sum(xs))
+    # one replication passes the obstacle and stops: min(1, 8 - 4) = 1
+    assert oracle.sneakysnake_partitioned(read, ref, 0, t, 1) == 1
+
+
+@pytest.mark.parametrize("E", [0, 1, 2, 3])
+def test_partitioned_special_cases_exhaustive(exhaustive_5, E):
+    reads, refs = exhaustive_5
+    P = ArrayPairs(reads, refs, E)
+    ss = np.minimum(oracle.int_batch("ss_full", P), E + 1)
+    wf = oracle.int_batch("wf", P)
+    # one sub-matrix with enough replications is the whole problem
+    assert np.array_equal(oracle.int_batch("ss_partitioned", P, p0=5, p1=5), ss)
+    # t = 1: a column costs an obstacle exactly when all 2E+1 cells block it
+    maps = [oracle.neighborhood_map(r.tobytes(), f.tobytes(), E) for r, f in
+            zip(reads[::97], refs[::97])]
+    blocked = np.array([int(np.all(M == 1, axis=0).sum()) for M in maps])
+    sub = ArrayPairs(reads[::97], refs[::97], E)
+    assert np.array_equal(oracle.int_batch("ss_partitioned", sub, p0=1, p1=1),
+                          np.minimum(blocked, E + 1))
+    prev = None
+    for t in (1, 2, 3, 5):
+        for y in (1, 2, 3, 6):
+            c = oracle.int_batch("ss_partitioned", P, p0=t, p1=y)
+            # restarting at sub-matrix borders and capping the replications
+            # only removes obstacles: never above SneakySnake or the distance
+            assert np.all(c <= ss) and np.all(c <= np.minimum(wf, E + 1))
+            if prev is not None and prev[0] == t:
+                assert np.all(c >= prev[1])  # more replications find more
+            prev = (t, c)
+
+
+def test_shouji_example_bit_vector():
+    kv, _ = read_golden("shouji_example.txt")
+    E = int(kv["E"])
+    v, ones = oracle.shouji_vector(kv["pattern"], kv["text"], E)
+    # zeros of the bit-vector are the common subsequences of Fig. 6.1
+    runs, i = [], 0
+    while i < len(v):
+        if v[i] == 0:
+            j = i
+            while j < len(v) and v[j] == 0:
+                j += 1
+            runs.append(kv["text"][i:j])
+            i = j
+        else:
+            i += 1
+    assert runs == kv["subsequences"].split(",")
+    assert ones == 3 and oracle.shouji(kv["pattern"], kv["text"], E) == 3
+
+
+@pytest.mark.parametrize("E", [0, 1, 2, 3])
+def test_shouji_zero_false_rejects_exhaustive(exhaustive_5, E):
+    reads, refs = exhaustive_5
+    P = ArrayPairs(reads, refs, E)
+    sh = oracle.int_batch("shouji", P)
+    wf = oracle.int_batch("wf", P)
+    # Ch. 6 analysis: similar sequences are never filtered out
+    assert np.all(sh <= np.minimum(wf, E + 1))
+    if E == 0:
+        exact = np.all(reads == refs, axis=1) & np.all(reads != ord("N"), axis=1)
+        assert np.array_equal(sh == 0, exact)
+
+
+def test_shouji_zero_false_rejects_synthetic():
+    for m, E, kind, km in ((100, 5, synth.UNIFORM, 20), (150, 6, synth.SKEWED, 60)):
+        P = synth.generate(kind, 0x5EED0100 + m, 400, m=m, E=E, kmax=km)
+        sh = oracle.int_batch("shouji", P)
+        wf = oracle.int_batch("wf", P)
+        assert np.all(sh <= np.minimum(wf, E + 1))
+
+
+def test_shd_streak_example():
+    kv, _ = read_golden("shd_streak_example.txt")
+    E = int(kv["E"])
+    assert oracle.gatekeeper_shd(kv["read"], kv["ref"], E, False, False) == int(kv["popcount_count"])
+    assert oracle.gatekeeper_shd(kv["read"], kv["ref"], E, False, True) == int(kv["streak_count"])
+    assert oracle.wf(kv["read"], kv["ref"]) == int(kv["edit_distance"])
+
+
+@pytest.mark.parametrize("E", [0, 1, 2, 3])
+def test_shd_switches_exhaustive(exhaustive_5, E):
+    reads, refs = exhaustive_5
+    P = ArrayPairs(reads, refs, E)
+    _, cnt = oracle.filter_batch(P)
+    gk = cnt[1].astype(np.int32)
+    assert np.array_equal(oracle.int_batch("gk_shd", P, p0=0, p1=0), gk)
+    vz = oracle.int_batch("gk_shd", P, p0=1, p1=0)
+    st = oracle.int_batch("gk_shd", P, p0=0, p1=1)
+    both = oracle.int_batch("gk_shd", P, p0=1, p1=1)
+    # zero-filled vacant cells and streak counting only lower the count
+    assert np.all(vz <= gk) and np.all(st <= gk) and np.all(both <= np.minimum(vz, st))
+    # the Hamming fast path is shared: within E, every variant reports it
+    ham = oracle.int_batch("hamming", P)
+    sel = ham <= E
+    assert np.array_equal(both[sel], ham[sel])
+
+
+def test_shouji_window_width_example():
+    kv, _ = read_golden("shouji_width_example.txt")
+    v, ones = oracle.shouji_vector(kv["read"], kv["ref"], int(kv["E"]))
+    assert "".join(str(int(b)) for b in v) == kv["bit_vector"]
+    assert ones == int(kv["count"])
+    assert oracle.wf(kv["read"], kv["ref"]) == int(kv["edit_distance"])
+
+
+def test_shd_vacant_zero_closed_form():
+    # reads that mismatch everywhere: every mask is all ones except its
+    # vacant cells, which SHD's shifts fill with 0, so the first E and the
+    # last E columns of the final bit-vector are 0 (Ch. 3, Leading and
+    # Trailing Zeros) and the count is m - 2E; with vacant cells 1 it is m
+    for m, E in ((8, 3), (10, 3), (12, 4)):
+        read, ref = "A" * m, "C" * m
+        assert oracle.gatekeeper_shd(read, ref, E, True, False) == min(m - 2 * E, E + 1)
+        assert oracle.gatekeeper_shd(read, ref, E, False, False) == E + 1
+        assert oracle.gatekeeper(read, ref, E) == E + 1
+        # one streak of m - 2E ones
+        assert oracle.gatekeeper_shd(read, ref, E, True, True) == min((m - 2 * E + 2) // 3, E + 1)
