@@ -228,6 +228,50 @@ PF_API pf_status pf_compact(pf_ctx *ctx, const uint8_t *flags, int64_t n,
 PF_API pf_status pf_compact_noalloc(const uint8_t *flags, int64_t n, int64_t *idx,
                                     int64_t *n_out, void *stream);
 
+/* ---- The thesis's other deciders on the same neighbourhood map ---------- */
+
+/* The three calls below take the arguments of pf_filter (one decider, one
+ * output slot: accept[n] and count[n], count = min(edits, E+1), accept =
+ * count <= E; a pair with len < 0 or E outside [0, E_max] gets count -1,
+ * accept 0 and makes pf_sync report PF_EINVAL).  Asynchronous on the
+ * context stream; caller-owned device buffers.  Per pair one thread builds
+ * the map a word at a time. */
+
+/* SneakySnake on sub-matrices (§8.5): the map is cut into non-overlapping
+ * sub-matrices of t columns (1 <= t <= 32; the last one holds what is
+ * left), each solved as its own Sneaky Snake Problem: the snake enters its
+ * first column free to pick any row, a pipe that reaches its last column
+ * leaves it, and at most y >= 1 replications (searches) run in it, so it
+ * contributes min(y, its obstacles).  The count is the sum over the
+ * sub-matrices; never above SneakySnake's, so no pair within E is
+ * rejected.  PF_EINVAL for t or y out of range. */
+PF_API pf_status pf_filter_partitioned(pf_ctx *ctx, const pf_pairs *pairs, const int32_t *lens,
+                                       const int16_t *E, int E_max, int t, int y,
+                                       uint8_t *accept, int16_t *count, int64_t n);
+
+/* Shouji (Ch. 6): for each of the m windows of 4 columns, the diagonal
+ * 4-bit vector with the most zeros (ties: the first, in diagonal order
+ * d = -E..E, whose first bit is 0, else the first) replaces the Shouji
+ * bit-vector's four bits there when it holds more zeros than they do; the
+ * bit-vector starts all ones, window cells past the end read as 1, and the
+ * count is the ones left in the bit-vector. */
+PF_API pf_status pf_filter_shouji(pf_ctx *ctx, const pf_pairs *pairs, const int32_t *lens,
+                                  const int16_t *E, int E_max, uint8_t *accept, int16_t *count,
+                                  int64_t n);
+
+/* GateKeeper with SHD's conventions (Ch. 3), for accuracy comparisons:
+ *   PF_SHD_VACANT_ZERO  out-of-range cells of the shifted masks are 0 (as
+ *                       SHD's arithmetic shifts fill them) instead of 1;
+ *   PF_SHD_STREAK       each maximal run of L ones of the final bit-vector
+ *                       counts ceil(L/3) edits (SHD's conservative counting
+ *                       charges three consecutive ones as one edit).
+ * flags = 0 gives GateKeeper's count; other bits are PF_EINVAL. */
+#define PF_SHD_VACANT_ZERO 1u
+#define PF_SHD_STREAK 2u
+PF_API pf_status pf_filter_shd(pf_ctx *ctx, const pf_pairs *pairs, const int32_t *lens,
+                               const int16_t *E, int E_max, unsigned flags, uint8_t *accept,
+                               int16_t *count, int64_t n);
+
 /* ---- a6: verification ---------------------------------------------------- */
 
 /* dist = min(Levenshtein(read, ref), E + 1) for the selected pairs, exact.

@@ -22,11 +22,15 @@ __all__ = [
     "pf_kernel_configs", "pf_tune_set", "pf_tune_get", "pf_tune", "pf_compact_noalloc",
     "ServeConfig", "Request", "pf_serve_start", "pf_submit", "pf_poll", "pf_wait",
     "pf_serve_resume", "pf_serve_stats_get", "pf_serve_stop", "pf_serve_replay", "pf_run_host",
+    "pf_filter_partitioned", "pf_filter_shouji", "pf_filter_shd", "PF_SHD_VACANT_ZERO",
+    "PF_SHD_STREAK",
 ]
 
 PF_SNEAKYSNAKE = 1
 PF_GATEKEEPER = 2
 PF_MAX_E = 31
+PF_SHD_VACANT_ZERO = 1
+PF_SHD_STREAK = 2
 
 _STATUS = {0: "PF_OK", 1: "PF_EINVAL", 2: "PF_ENOMEM", 3: "PF_ECUDA", 4: "PF_ETIMEOUT",
            5: "PF_EBUSY", 6: "PF_ECANCELLED", 7: "PF_EDATA"}
@@ -102,6 +106,9 @@ def load():
         "pf_pack_fixed": [P, P, I64, I, P, P, P],
         "pf_filter": [P, U, ctypes.POINTER(_Pairs), P, P, I, P, P, I64],
         "pf_filter_plain": [P, U, ctypes.POINTER(_Pairs), P, P, I, P, P, I64],
+        "pf_filter_partitioned": [P, ctypes.POINTER(_Pairs), P, P, I, I, I, P, P, I64],
+        "pf_filter_shouji": [P, ctypes.POINTER(_Pairs), P, P, I, P, P, I64],
+        "pf_filter_shd": [P, ctypes.POINTER(_Pairs), P, P, I, U, P, P, I64],
         "pf_compact": [P, P, I64, P, P],
         "pf_compact_noalloc": [P, I64, P, P, P],
         "pf_verify": [P, ctypes.POINTER(_Pairs), P, P, I, P, P, I64, P],
@@ -284,6 +291,35 @@ def pf_filter(ctx, deciders, pairs, lens, E, E_max, accept, count, n=None):
 def pf_filter_plain(ctx, deciders, pairs, lens, E, E_max, accept, count, n=None):
     n = lens.numel() if n is None else n
     _filter_call(load().pf_filter_plain, ctx, deciders, pairs, lens, E, E_max, accept, count, n)
+
+
+def _variant_call(fn, ctx, pairs, lens, E, E_max, extra, accept, count, n):
+    _dt(lens, torch.int32, "lens")
+    _dt(E, torch.int16, "E")
+    _dt(accept, torch.uint8, "accept")
+    _dt(count, torch.int16, "count")
+    n = lens.numel() if n is None else n
+    _cur_stream(ctx)
+    cp = pairs._c()
+    _check(fn(ctx.handle, ctypes.byref(cp), _p(lens), _p(E), int(E_max), *extra, _p(accept),
+              _p(count), int(n)), ctx.handle)
+
+
+def pf_filter_partitioned(ctx, pairs, lens, E, E_max, t, y, accept, count, n=None):
+    """SneakySnake on sub-matrices of t columns with y replications each."""
+    _variant_call(load().pf_filter_partitioned, ctx, pairs, lens, E, E_max, (int(t), int(y)),
+                  accept, count, n)
+
+
+def pf_filter_shouji(ctx, pairs, lens, E, E_max, accept, count, n=None):
+    """Shouji: 4-column windows and the Shouji bit-vector."""
+    _variant_call(load().pf_filter_shouji, ctx, pairs, lens, E, E_max, (), accept, count, n)
+
+
+def pf_filter_shd(ctx, pairs, lens, E, E_max, flags, accept, count, n=None):
+    """GateKeeper with SHD's vacant-zero masks and/or streak counting."""
+    _variant_call(load().pf_filter_shd, ctx, pairs, lens, E, E_max, (int(flags),), accept,
+                  count, n)
 
 
 def pf_compact(ctx, flags, idx, n_out, n=None):
