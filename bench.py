@@ -468,6 +468,31 @@ def main_gpu(args):
     # headline comparison: SneakySnake alone, batched (tuned) vs plain kernel
     ss_batched_ms = timed(lambda: pf.pf_filter(ctx, 1, pairs, lens, E, E_HEAD, acc, cnt, n))
     ss_plain_ms = timed(lambda: pf.pf_filter_plain(ctx, 1, pairs, lens, E, E_HEAD, acc, cnt, n))
+
+    # The thesis's other deciders on the same batch: throughput, and accuracy
+    # against the exact distances of the step (SneakySnake never rejects a
+    # pair within E, so every pair it rejected is beyond E).
+    pf.pf_filter_verify(ctx, 3, pairs, lens, E, E_HEAD, acc, cnt, dist_out, n)
+    truth = dist_out <= E_HEAD
+    n_far = int((~truth).sum().item())
+
+    def accuracy(a):
+        a = a.bool()
+        return {"accept_frac": a.float().mean().item(),
+                "false_accept_rate": int((a & ~truth).sum().item()) / max(n_far, 1),
+                "false_rejects": int((truth & ~a).sum().item())}
+
+    variants = {"sneakysnake": accuracy(acc[:n]), "gatekeeper": accuracy(acc[n:2 * n])}
+    v_reps = max(3, args.steps // 5)
+    for name, fn, extra in (("sneakysnake_t8_y2", pf.pf_filter_partitioned, (8, 2)),
+                            ("sneakysnake_t32_y32", pf.pf_filter_partitioned, (32, 32)),
+                            ("shouji", pf.pf_filter_shouji, ()),
+                            ("gatekeeper_shd", pf.pf_filter_shd,
+                             (pf.PF_SHD_VACANT_ZERO | pf.PF_SHD_STREAK,))):
+        v_ms = timed(lambda: fn(ctx, pairs, lens, E, E_HEAD, *extra, acc[:n], cnt[:n], n),
+                     reps=v_reps)
+        variants[name] = dict(accuracy(acc[:n]), pairs_s=n / (v_ms / 1000.0), ms=v_ms)
+    variants["sneakysnake"]["pairs_s"] = n / (ss_batched_ms / 1000.0)
     pf.pf_sync(ctx)
 
     # end to end through the public API: pf_run_host on pinned host ASCII,
@@ -553,6 +578,7 @@ def main_gpu(args):
                                "plain_pairs_s": n / (ss_plain_ms / 1000.0),
                                "batched_over_plain": ss_plain_ms / ss_batched_ms,
                                "tuned_cfg": list(tuned[1])},
+        "deciders": variants,
         "roofline": roof,
         "e2e": {"value": total / (e2e_ms / 1000.0), "unit": "pairs/s", "ms_per_step": e2e_ms,
                 "call": "pf_run_host (pinned host buffers, 1M-pair chunks, graph replay)",
@@ -563,9 +589,12 @@ def main_gpu(args):
         "clocks": clk,
         "gen_s": t_gen,
     }
-    # kernels of ours launched per step: 2 pack + bin init + filter +
-    # 3 compaction + fill + verify
-    line["gpu_launches"] = args.steps * 9
+    # kernels of ours launched per step: 2 pack, binning (init, and with
+    # several configurations histogram, scan, scatter), one filter launch per
+    # distinct configuration serving E = 0..E_HEAD (a per-pair E array can
+    # hold any of them), 3 compaction, 1 verification
+    n_cfg = len({pf.pf_tune_get(ctx, 3, e)[0] for e in range(E_HEAD + 1)})
+    line["gpu_launches"] = args.steps * (2 + (1 if n_cfg == 1 else 4) + n_cfg + 3 + 1)
     if rank == 0 and world == 1 and not args.no_cpu:
         r, dt, thr = oracle_step_rate(args.cpu_sample)
         line["cpu_baseline"] = {"value": r, "unit": "pairs/s", "cores": thr, "kind": "oracle",
