@@ -537,9 +537,9 @@ def main_gpu(args):
     # DRAM bytes per launch from one ncu capture of each kernel at 2M pairs
     # (profiles/), scaled to this launch by the units processed; valid for
     # the kernels as captured (filter<1,7,3,6>, pack_fixed, verify<u32>)
-    traffic_per_pair = {"filter": (248.020992e6 + 10.175744e6) / 2e6,
-                        "pack": 2 * (300.049152e6 + 95.794944e6) / 4e6,
-                        "verify": (249.872384e6 + 6.593024e6) / 2e6}
+    traffic_per_pair = {"filter": (248.055552e6 + 10.317568e6) / 2e6,
+                        "pack": 2 * (300.0896e6 + 95.116544e6) / 4e6,
+                        "verify": (224.882944e6 + 6.427648e6) / 2e6}
     sm_mhz = clk.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
     alu_peak = 152 * 64 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # Top/s, ALU pipe
     ms_dom = stages[dominant]
