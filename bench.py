@@ -145,7 +145,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    n_sample = args.cpu_sample
+    n_sample = args.ref_sample
     times = []
     rate = None
     for i in range(args.warmup + args.steps):
@@ -615,7 +615,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--pairs", type=int, default=N_PAIRS)
-    ap.add_argument("--cpu-sample", type=int, default=400_000)
+    ap.add_argument("--cpu-sample", type=int, default=8_000_000,
+                    help="pairs of the oracle's timed sample for cpu_baseline (about 10 s)")
+    ap.add_argument("--ref-sample", type=int, default=400_000,
+                    help="pairs per step of --impl reference (K + W steps in a few minutes)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default kernel choice")
     ap.add_argument("--no-extras", action="store_true",

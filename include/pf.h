@@ -185,6 +185,14 @@ PF_API pf_status pf_filter_plain(pf_ctx *ctx, unsigned deciders, const pf_pairs 
 PF_API pf_status pf_kernel_configs(int *tpp, int *dpt, int *ecap, int *exact_e, int cap,
                                    int *count);
 
+/* Batches of fewer than `pairs` pairs skip the scheduler: one launch of the
+ * plain one-thread-per-pair kernel serving E_max, no binning and no
+ * per-threshold launches, whose fixed costs dominate small batches.
+ * Default 2^20; 0 sends every batch of pf_filter / pf_filter_verify /
+ * pf_run_host through the batched scheduler.  pf_tune always times the
+ * batched scheduler.  PF_EINVAL for pairs < 0. */
+PF_API pf_status pf_set_small_batch(pf_ctx *ctx, int64_t pairs);
+
 /* Use configuration cfg and a work chunk of `chunk` pairs (1..65536) for
  * threshold E under decider set `deciders` in later pf_filter calls.
  * PF_EINVAL if cfg cannot serve E. */

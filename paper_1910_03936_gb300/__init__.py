@@ -23,7 +23,7 @@ __all__ = [
     "ServeConfig", "Request", "pf_serve_start", "pf_submit", "pf_poll", "pf_wait",
     "pf_serve_resume", "pf_serve_stats_get", "pf_serve_stop", "pf_serve_replay", "pf_run_host",
     "pf_filter_partitioned", "pf_filter_shouji", "pf_filter_shd", "PF_SHD_VACANT_ZERO",
-    "PF_SHD_STREAK",
+    "PF_SHD_STREAK", "pf_set_small_batch",
 ]
 
 PF_SNEAKYSNAKE = 1
@@ -124,6 +124,7 @@ def load():
         "pf_run_host": [P, U, P, P, P, I, P, I, P, P, P, I64, I64],
         "pf_serve_replay": [P, P, I, P, I, P, ctypes.POINTER(ctypes.c_double)],
         "pf_tune_set": [P, U, I, I, I],
+        "pf_set_small_batch": [P, I64],
         "pf_tune_get": [P, U, I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
         "pf_tune": [P, U, ctypes.POINTER(_Pairs), P, I, I64, I, ctypes.POINTER(ctypes.c_int),
                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)],
@@ -416,6 +417,11 @@ def pf_kernel_configs():
 
 def pf_tune_set(ctx, deciders, E, cfg, chunk):
     _check(load().pf_tune_set(ctx.handle, int(deciders), int(E), int(cfg), int(chunk)), ctx.handle)
+
+
+def pf_set_small_batch(ctx, pairs):
+    """Batches below `pairs` take one plain launch (0: always the scheduler)."""
+    _check(load().pf_set_small_batch(ctx.handle, int(pairs)), ctx.handle)
 
 
 def pf_tune_get(ctx, deciders, E):

@@ -469,16 +469,29 @@ pf_status pf_pack_fixed(pf_ctx *ctx, const uint8_t *ascii, int64_t nseq, int len
                      "pack launch");
 }
 
+// The plain kernel serving E_max: the first with DPT - 1 >= E_max.
+static int plain_index(int E_max) {
+    int pi = 0;
+    while (pi < kNumPlain && kPlainDpt[pi] - 1 < E_max) ++pi;
+    return pi;
+}
+
+pf_status pf_ctx::run_filter(unsigned dec, const FilterArgs &a, const Scratch &s) {
+    if (a.n < small_batch)  // fixed costs of binning and per-bin launches dominate
+        return cuda(launch_filter_plain((int)dec, plain_index(a.E_max), a, stream),
+                    "filter launch");
+    return run_batched(dec, a, s);
+}
+
 pf_status pf_filter_plain(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs,
                           const int32_t *lens, const int16_t *E, int E_max, uint8_t *accept,
                           int16_t *count, int64_t n) {
     pf_status st = check_filter_args(ctx, deciders, pairs, lens, E_max, accept, count, n);
     if (st != PF_OK || n == 0) return st;
     cudaSetDevice(ctx->device);
-    int pi = 0;
-    while (pi < kNumPlain && kPlainDpt[pi] - 1 < E_max) ++pi;
     const FilterArgs a = make_filter_args(ctx, pairs, lens, E, E_max, accept, count, n);
-    return ctx->cuda(launch_filter_plain((int)deciders, pi, a, ctx->stream), "filter launch");
+    return ctx->cuda(launch_filter_plain((int)deciders, plain_index(E_max), a, ctx->stream),
+                     "filter launch");
 }
 
 pf_status pf_filter(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs, const int32_t *lens,
@@ -490,7 +503,7 @@ pf_status pf_filter(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs, const
     st = ctx->scratch_layout(n, &s);
     if (st != PF_OK) return st;
     const FilterArgs a = make_filter_args(ctx, pairs, lens, E, E_max, accept, count, n);
-    return ctx->run_batched(deciders, a, s);
+    return ctx->run_filter(deciders, a, s);
 }
 
 pf_status pf_compact(pf_ctx *ctx, const uint8_t *flags, int64_t n, int64_t *idx,
@@ -534,7 +547,7 @@ pf_status pf_filter_verify(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs
     if (st != PF_OK) return st;
     FilterArgs a = make_filter_args(ctx, pairs, lens, E, E_max, accept, count, n);
     a.dist = dist;  // the filter writes E + 1 for the pairs it rejects
-    st = ctx->run_batched(deciders, a, s);
+    st = ctx->run_filter(deciders, a, s);
     if (st != PF_OK) return st;
     // the first selected decider's accept flags choose the pairs to verify
     st = ctx->cuda(launch_compact(accept, n, s.idx, s.n_idx, s.tiles, ctx->stream),
@@ -554,6 +567,13 @@ pf_status pf_kernel_configs(int *tpp, int *dpt, int *ecap, int *exact_e, int cap
         if (exact_e) exact_e[c] = kBatchCfgs[c].xe;
     }
     *count = kNumBatchCfgs;
+    return PF_OK;
+}
+
+pf_status pf_set_small_batch(pf_ctx *ctx, int64_t pairs) {
+    if (!ctx) return PF_EINVAL;
+    if (pairs < 0) return ctx->fail(PF_EINVAL, "pf_set_small_batch: pairs < 0");
+    ctx->small_batch = pairs;
     return PF_OK;
 }
 

@@ -46,6 +46,9 @@ struct pf_ctx {
     // tuned kernel per decider set and threshold
     int tune_cfg[4][PF_MAX_E + 1];
     int tune_chunk[4][PF_MAX_E + 1];
+    // batches of fewer pairs take one plain launch (no binning, no per-bin
+    // launches); 0 sends every batch through the batched scheduler
+    int64_t small_batch = int64_t(1) << 20;
     int grid_cache[4][pf::kNumBatchCfgs] = {};
 
     cudaStream_t side_streams[pf::kSideStreams] = {};
@@ -61,6 +64,8 @@ struct pf_ctx {
     int grid_for(int dec, int cfg);
     void reset_tuning();
     pf_status run_batched(unsigned dec, const pf::FilterArgs &a, const pf::Scratch &s);
+    // run_batched, or one plain launch for a batch below small_batch
+    pf_status run_filter(unsigned dec, const pf::FilterArgs &a, const pf::Scratch &s);
 };
 
 void pf_serve_teardown(pf_ctx *ctx);

@@ -173,7 +173,7 @@ pf_status enqueue_chunk(Job &J, Slot &s, int64_t nc) {
     a.dist = s.dist;  // E + 1 for the pairs the filter rejects
     cudaStream_t saved = ctx->stream;
     ctx->stream = s.st;
-    pf_status st = ctx->run_batched(J.dec, a, s.scr);
+    pf_status st = ctx->run_filter(J.dec, a, s.scr);
     ctx->stream = saved;
     if (st != PF_OK) return st;
     e = launch_compact(s.acc, nc, s.scr.idx, s.scr.n_idx, s.scr.tiles, s.st);

@@ -28,6 +28,7 @@ def pf():
 @pytest.fixture(scope="module")
 def ctx(pf):
     c = pf.pf_create(0)
+    pf.pf_set_small_batch(c, 0)  # these batches are small: exercise the scheduler's kernels
     yield c
     pf.pf_destroy(c)
 
@@ -416,3 +417,26 @@ def test_tuner_picks_a_valid_config_and_stays_exact(pf, ctx, case_data):
     assert pf.pf_tune_get(ctx, 3, 6) == (cfg, chunk)
     a, c = filter_dev(ctx, D, 3)
     assert np.array_equal(c, oc) and np.array_equal(a, oa)
+
+
+def test_small_batches_take_one_plain_launch(pf, case_data):
+    """With the default small-batch rule, pf_filter and pf_filter_verify on
+    small batches run the plain kernel; results are the same."""
+    P, D, (oa, oc) = case_data["cfg3_mixed"]
+    c = pf.pf_create(0)
+    try:
+        from gpu_util import filter_dev
+        a, k = filter_dev(c, D, 3)
+        assert np.array_equal(a, oa) and np.array_equal(k, oc)
+        n = D.n
+        acc = torch.zeros(2 * n, dtype=torch.uint8, device="cuda:0")
+        cnt = torch.zeros(2 * n, dtype=torch.int16, device="cuda:0")
+        dist = torch.full((n,), -5, dtype=torch.int32, device="cuda:0")
+        pf.pf_filter_verify(c, 3, D.pairs, D.lens, D.E, D.E_max, acc, cnt, dist, n)
+        pf.pf_sync(c)
+        want = np.where(oa[0] == 1, oracle.verify_batch(P), P.E.astype(np.int32) + 1)
+        assert np.array_equal(dist.cpu().numpy(), want)
+        with pytest.raises(pf.PFError):
+            pf.pf_set_small_batch(c, -1)
+    finally:
+        pf.pf_destroy(c)
