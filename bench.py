@@ -465,6 +465,11 @@ def main_gpu(args):
     compact_ms = timed(lambda: pf.pf_compact(ctx, acc[:n], idx, n_idx, n))
     verify_ms = timed(lambda: pf.pf_verify(ctx, pairs, lens, E, E_HEAD, idx, n_idx, dist_out, n))
     n_verified = int(n_idx.item())
+    # the alternative to filtering: the early-exit verifier on every pair
+    dist_all = torch.empty(n, dtype=torch.int32, device=dev)
+    verify_all_ms = timed(lambda: pf.pf_verify(ctx, pairs, lens, E, E_HEAD, None, None,
+                                               dist_all, n))
+    del dist_all
     # headline comparison: SneakySnake alone, batched (tuned) vs plain kernel
     ss_batched_ms = timed(lambda: pf.pf_filter(ctx, 1, pairs, lens, E, E_HEAD, acc, cnt, n))
     ss_plain_ms = timed(lambda: pf.pf_filter_plain(ctx, 1, pairs, lens, E, E_HEAD, acc, cnt, n))
@@ -572,7 +577,8 @@ def main_gpu(args):
                    "deciders": "SneakySnake+GateKeeper", "verify": "SneakySnake accepts",
                    "l2": "inputs larger than L2 (9 GB resident)"},
         "stages_ms": {"pack": pack_ms, "filter_compact_verify": fv_ms, "filter": filt_ms,
-                      "compact": compact_ms, "verify": verify_ms},
+                      "compact": compact_ms, "verify": verify_ms,
+                      "verify_all_pairs_instead": verify_all_ms},
         "accepted_frac": n_verified / n,
         "filter_sneakysnake": {"batched_pairs_s": n / (ss_batched_ms / 1000.0),
                                "plain_pairs_s": n / (ss_plain_ms / 1000.0),
