@@ -541,8 +541,9 @@ def main_gpu(args):
     }
     # DRAM bytes per launch from one ncu capture of each kernel at 2M pairs
     # (profiles/), scaled to this launch by the units processed; valid for
-    # the kernels as captured (filter<1,7,3,6>, pack_fixed, verify<u32>)
-    traffic_per_pair = {"filter": (248.055552e6 + 10.317568e6) / 2e6,
+    # the kernels as captured (the two-phase exact-E6 filter the tuner picks,
+    # pack_fixed, verify<u32>)
+    traffic_per_pair = {"filter": (248.083456e6 + 10.464e6) / 2e6,
                         "pack": 2 * (300.0896e6 + 95.116544e6) / 4e6,
                         "verify": (224.882944e6 + 6.427648e6) / 2e6}
     sm_mhz = clk.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)

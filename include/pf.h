@@ -179,11 +179,16 @@ PF_API pf_status pf_filter_plain(pf_ctx *ctx, unsigned deciders, const pf_pairs 
 /* ---- a7: scheduler tuning --------------------------------------------------- */
 
 /* Kernel configurations of the batch scheduler.  Writes up to cap entries
- * (lanes per pair, diagonal slots per lane, largest E served, and the one
- * E an exact-threshold configuration serves or -1) into the host arrays
- * (any may be NULL) and the number of configurations into *count. */
-PF_API pf_status pf_kernel_configs(int *tpp, int *dpt, int *ecap, int *exact_e, int cap,
-                                   int *count);
+ * (lanes per pair, diagonal slots per lane, largest E served, the one E an
+ * exact-threshold configuration serves or -1, and for the two-phase form
+ * the pair length in 32-column words up to which its mask words stay in
+ * shared memory, else 0) into the host arrays (any may be NULL) and the
+ * number of configurations into *count.  The two-phase form builds every
+ * word's mask words (and runs GateKeeper) first, then runs SneakySnake as a
+ * per-thread loop of steps over them; longer pairs, and GateKeeper alone,
+ * take the fused word loop. */
+PF_API pf_status pf_kernel_configs(int *tpp, int *dpt, int *ecap, int *exact_e, int *words,
+                                   int cap, int *count);
 
 /* Batches of fewer than `pairs` pairs skip the scheduler: one launch of the
  * plain one-thread-per-pair kernel serving E_max, no binning and no

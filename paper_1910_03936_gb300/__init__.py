@@ -113,7 +113,7 @@ def load():
         "pf_compact_noalloc": [P, I64, P, P, P],
         "pf_verify": [P, ctypes.POINTER(_Pairs), P, P, I, P, P, I64, P],
         "pf_filter_verify": [P, U, ctypes.POINTER(_Pairs), P, P, I, P, P, P, I64],
-        "pf_kernel_configs": [P, P, P, P, I, ctypes.POINTER(ctypes.c_int)],
+        "pf_kernel_configs": [P, P, P, P, P, I, ctypes.POINTER(ctypes.c_int)],
         "pf_serve_start": [P, ctypes.POINTER(ServeConfig)],
         "pf_submit": [P, ctypes.POINTER(_Request), ctypes.POINTER(ctypes.c_uint64)],
         "pf_poll": [P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)],
@@ -404,12 +404,14 @@ def pack_pairs(ctx, reads, refs, length=None, byte_off=None):
 
 
 def pf_kernel_configs():
-    """List of (tpp, dpt, ecap, exact_e) of the batch scheduler's kernels;
-    exact_e >= 0 marks a kernel that serves that threshold only."""
+    """List of (tpp, dpt, ecap, exact_e, words) of the batch scheduler's
+    kernels; exact_e >= 0 marks a kernel that serves that threshold only,
+    words > 0 its two-phase form (mask words of pairs up to that many
+    32-column words kept in shared memory)."""
     import numpy as np
     cnt = ctypes.c_int()
-    _check(load().pf_kernel_configs(None, None, None, None, 0, ctypes.byref(cnt)))
-    a = [np.zeros(cnt.value, dtype=np.int32) for _ in range(4)]
+    _check(load().pf_kernel_configs(None, None, None, None, None, 0, ctypes.byref(cnt)))
+    a = [np.zeros(cnt.value, dtype=np.int32) for _ in range(5)]
     _check(load().pf_kernel_configs(*[ctypes.c_void_p(x.ctypes.data) for x in a], cnt.value,
                                     ctypes.byref(cnt)))
     return [tuple(int(x[i]) for x in a) for i in range(cnt.value)]

@@ -180,16 +180,22 @@ int pf_ctx::grid_for(int dec, int cfg) {
     int &g = grid_cache[dec][cfg];
     if (g == 0) {
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, filter_batched_fn(dec, cfg), 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, filter_batched_fn(dec, cfg),
+                                                      cfg_threads(kBatchCfgs[cfg], dec),
+                                                      cfg_smem(kBatchCfgs[cfg], dec));
         g = std::max(1, per_sm) * sms;
     }
     return g;
 }
 
 // Default configuration for threshold E before any tuning: the
-// exact-threshold one-thread kernel up to E = 15, eight lanes per pair
-// above.
+// exact-threshold one-thread kernel up to E = 15 (its two-phase form for
+// E = 3..7, whose shared arrays hold pairs up to 256 bases), eight lanes
+// per pair above.
 int pf::pf_default_cfg(int E) {
+    if (E >= 3 && E <= 7)
+        for (int c = 0; c < kNumBatchCfgs; ++c)
+            if (kBatchCfgs[c].xe == E && kBatchCfgs[c].words >= 8) return c;
     if (E <= 15) return kFirstExactCfg + E;
     for (int c = 0; c < kNumBatchCfgs; ++c)
         if (kBatchCfgs[c].tpp == 8 && kBatchCfgs[c].xe < 0 && kBatchCfgs[c].ecap >= E) return c;
@@ -296,7 +302,9 @@ pf_status pf_ctx::run_batched(unsigned dec, const FilterArgs &a, const Scratch &
         const int c = used[0];
         b.chunk = tune_chunk[dec][a.E_max];
         const int64_t items = (a.n + b.chunk - 1) / b.chunk;
-        const int grid = (int)std::min<int64_t>(grid_for(dec, c), std::max<int64_t>(1, (items + 7) / 8));
+        const int wpb = cfg_threads(kBatchCfgs[c], (int)dec) / 32;  // warps per block
+        const int grid = (int)std::min<int64_t>(grid_for(dec, c),
+                                                std::max<int64_t>(1, (items + wpb - 1) / wpb));
         return cuda(launch_filter_batched(dec, c, grid, b, c, stream), "filter launch");
     }
     // several configurations: one persistent launch each, concurrently
@@ -558,13 +566,15 @@ pf_status pf_filter_verify(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs
                      "verify launch");
 }
 
-pf_status pf_kernel_configs(int *tpp, int *dpt, int *ecap, int *exact_e, int cap, int *count) {
+pf_status pf_kernel_configs(int *tpp, int *dpt, int *ecap, int *exact_e, int *words, int cap,
+                            int *count) {
     if (!count || cap < 0) return PF_EINVAL;
     for (int c = 0; c < kNumBatchCfgs && c < cap; ++c) {
         if (tpp) tpp[c] = kBatchCfgs[c].tpp;
         if (dpt) dpt[c] = kBatchCfgs[c].dpt;
         if (ecap) ecap[c] = kBatchCfgs[c].ecap;
         if (exact_e) exact_e[c] = kBatchCfgs[c].xe;
+        if (words) words[c] = kBatchCfgs[c].words;
     }
     *count = kNumBatchCfgs;
     return PF_OK;

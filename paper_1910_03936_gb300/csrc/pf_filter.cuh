@@ -82,7 +82,11 @@ static __device__ uint32_t g_minus_one = 0xffffffffu;
 // processes one reference word and reports whether both deciders are
 // decided, finish() closes GateKeeper's last word.  Every lane of the
 // group holds the same copy of the scalar state.
-template <int TPP, int DPT, int DEC, int XE = -1, typename L = LdNC>
+// SINK: every word's mask words are also stored (at sink[(w * NS + k) * 32],
+// one lane's column of a per-warp array), and the words run to the end of
+// the pair whatever the deciders' state: the first phase of the two-phase
+// kernel below.
+template <int TPP, int DPT, int DEC, int XE = -1, typename L = LdNC, bool SINK = false>
 struct PairFilter {
     using SM = SlotMap<TPP, DPT, XE>;
     static constexpr int NS = SM::NS;
@@ -146,7 +150,12 @@ struct PairFilter {
         neg1 = *(volatile const uint32_t *)&g_minus_one;
     }
 
-    __device__ __forceinline__ bool done() const { return (ss_done && gk_done) || w >= W; }
+    uint32_t *sink;       // SINK only
+
+    __device__ __forceinline__ bool done() const {
+        if constexpr (SINK) return w >= W;
+        return (ss_done && gk_done) || w >= W;
+    }
 
     // Process every remaining word, then leave `role` for finish().
     __device__ __forceinline__ void run(const PairsView &pv, int g, unsigned gmask) {
@@ -207,6 +216,10 @@ struct PairFilter {
 #pragma unroll
             for (int k = 0; k < NS; ++k)
                 if (live(k, g)) M[k] &= valid;
+        }
+        if constexpr (SINK) {
+#pragma unroll
+            for (int k = 0; k < NS; ++k) sink[(w * NS + k) * 32] = M[k];
         }
 
         // ---- SneakySnake steps inside this word
@@ -444,6 +457,114 @@ __global__ void __launch_bounds__(256) filter_batched_kernel(BatchArgs b, int bi
         for (int64_t q = s + gid; q < e; q += GPW) {
             const int64_t p = order ? __ldg(order + q) : q;
             filter_group<TPP, DPT, DEC, XE>(b.f, p, g, gmask);
+        }
+    }
+}
+
+// ---- Two-phase form (exact threshold, one thread per pair) -----------------
+//
+// In the fused loop a warp runs, in every word, as many SneakySnake steps as
+// its busiest lane needs.  Here the first phase builds the mask words of the
+// whole pair (and runs GateKeeper) word by word, storing them in shared
+// memory; the second runs the snake as a per-lane loop of steps over the
+// stored words, so a warp runs as many steps as its busiest lane needs in
+// total.  The walk is the fused loop's, word for word: the same checkpoint
+// mask, the same carry of blocked diagonals into the next word.
+template <int XE>
+__device__ __forceinline__ int split_sneakysnake(const uint32_t *mine, int W, uint32_t neg1) {
+    constexpr int NS = 2 * XE + 1;
+    if (W == 0) return 0;
+    uint32_t Mw[NS];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) Mw[k] = mine[k * 32];
+    int ws = 0, kss = 0;
+    uint32_t C = 0xffffffffu, dead = 0u;
+    bool cont = false;
+    for (;;) {
+        uint32_t T = 0xffffffffu;
+        if (cont) {  // a pipe runs on from the previous word
+#pragma unroll
+            for (int k = 0; k < NS; ++k) {
+                const uint32_t y = Mw[k] | ((dead >> k) & 1u);
+                T &= y | (y * neg1);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < NS; ++k) {
+                const uint32_t y = Mw[k] & C;
+                T &= y | (y * neg1);
+            }
+        }
+        if (T == 0u) {  // the deepest pipe reaches the end of the word
+            if (ws == W - 1) break;
+            uint32_t dd = cont ? dead : 0u;
+#pragma unroll
+            for (int k = 0; k < NS; ++k)
+                if (Mw[k] & (cont ? 0xffffffffu : C)) dd |= 1u << k;
+            dead = dd;
+            cont = true;
+            ++ws;
+#pragma unroll
+            for (int k = 0; k < NS; ++k) Mw[k] = mine[(ws * NS + k) * 32];
+            continue;
+        }
+        const int pbit = __ffs(T) - 1;
+        ++kss;
+        cont = false;
+        if (kss > XE) break;
+        if (pbit == 31) {  // the obstacle was the word's last column
+            if (ws == W - 1) break;
+            ++ws;
+#pragma unroll
+            for (int k = 0; k < NS; ++k) Mw[k] = mine[(ws * NS + k) * 32];
+            C = 0xffffffffu;
+        } else {
+            C = 0xfffffffeu << pbit;
+        }
+    }
+    return kss > XE + 1 ? XE + 1 : kss;
+}
+
+template <int DEC, int XE, int WMAX>
+__device__ __forceinline__ void filter_split_pair(const FilterArgs &a, int64_t p, uint32_t *mine,
+                                                  unsigned lane_mask) {
+    int m, E;
+    if (!pair_args<1, XE + 1, DEC, XE>(a, p, 0, &m, &E)) return;
+    const int W = (m + 31) >> 5;
+    if (W > WMAX) {  // longer than the shared arrays: the fused loop
+        filter_group<1, XE + 1, DEC, XE>(a, p, 0, lane_mask);
+        return;
+    }
+    PairFilter<1, XE + 1, DEC & 2, XE, LdNC, true> st;
+    st.sink = mine;
+    st.init(a.pairs, p, m, E);
+    st.run(a.pairs, 0, lane_mask);
+    int ssc = 0, gkc = 0;
+    st.finish(0, lane_mask, &ssc, &gkc);
+    if constexpr (DEC & 1) ssc = split_sneakysnake<XE>(mine, W, st.neg1);
+    write_outputs<DEC>(a, p, E, ssc, gkc);
+}
+
+// Shared memory: kSplitWarps warps x WMAX words x (2 XE + 1) slots x 32 lanes.
+template <int DEC, int XE, int WMAX>
+__global__ void __launch_bounds__(kSplitWarps * 32) filter_split_kernel(BatchArgs b, int bin) {
+    extern __shared__ uint32_t split_maps[];
+    constexpr int NS = 2 * XE + 1;
+    const int lane = threadIdx.x & 31;
+    uint32_t *mine = split_maps + (threadIdx.x >> 5) * (WMAX * NS * 32) + lane;
+    const int64_t lo = b.bin_start[bin], hi = b.bin_start[bin + 1];
+    unsigned long long *counter = b.work + bin;
+    const int64_t *order = (b.order && !(b.ident && *b.ident)) ? b.order : nullptr;
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(counter, 1ull);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        const int64_t s = lo + (int64_t)item * b.chunk;
+        if (s >= hi) break;
+        const int64_t e = min(hi, s + (int64_t)b.chunk);
+        for (int64_t q = s + lane; q < e; q += 32) {
+            const int64_t p = order ? __ldg(order + q) : q;
+            filter_split_pair<DEC, XE, WMAX>(b.f, p, mine, 1u << lane);
         }
     }
 }

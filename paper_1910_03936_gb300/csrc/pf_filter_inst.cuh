@@ -13,13 +13,27 @@ using CfgAt = std::integral_constant<int, I>;
 template <int I>
 static const void *batched_ptr_i() {
     constexpr KernelCfg c = kBatchCfgs[I];
-    return reinterpret_cast<const void *>(&filter_batched_kernel<c.tpp, c.dpt, PF_DEC, c.xe>);
+    if constexpr (cfg_split(c, PF_DEC)) {
+        const void *f = reinterpret_cast<const void *>(&filter_split_kernel<PF_DEC, c.xe, c.words>);
+        static const cudaError_t attr = cudaFuncSetAttribute(
+            f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg_smem(c, PF_DEC));
+        (void)attr;
+        return f;
+    } else {
+        return reinterpret_cast<const void *>(&filter_batched_kernel<c.tpp, c.dpt, PF_DEC, c.xe>);
+    }
 }
 
 template <int I>
 static cudaError_t launch_batched_i(int grid, const BatchArgs &b, int bin, cudaStream_t st) {
     constexpr KernelCfg c = kBatchCfgs[I];
-    filter_batched_kernel<c.tpp, c.dpt, PF_DEC, c.xe><<<grid, 256, 0, st>>>(b, bin);
+    if constexpr (cfg_split(c, PF_DEC)) {
+        batched_ptr_i<I>();  // sets the shared-memory limit once
+        filter_split_kernel<PF_DEC, c.xe, c.words>
+            <<<grid, cfg_threads(c, PF_DEC), cfg_smem(c, PF_DEC), st>>>(b, bin);
+    } else {
+        filter_batched_kernel<c.tpp, c.dpt, PF_DEC, c.xe><<<grid, 256, 0, st>>>(b, bin);
+    }
     return cudaGetLastError();
 }
 

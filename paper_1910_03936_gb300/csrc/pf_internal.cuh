@@ -88,6 +88,9 @@ struct FilterArgs {
     int32_t *dist = nullptr;  // non-null: E + 1 for pairs the first decider rejects, -1 if invalid
 };
 
+// Warps per block of the two-phase filter kernel.
+constexpr int kSplitWarps = 4;
+
 // Batched (scheduler) launch: pairs taken in chunks from `order` (null:
 // identity) through a work counter.
 struct BatchArgs {

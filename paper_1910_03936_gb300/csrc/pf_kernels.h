@@ -10,9 +10,12 @@ namespace pf {
 
 // One batched-filter configuration: TPP lanes per pair, DPT diagonal slots
 // per lane; it serves thresholds E <= ecap.  xe >= 0 marks the
-// exact-threshold form (one thread per pair, serves E == xe only).
+// exact-threshold form (one thread per pair, serves E == xe only).  words
+// > 0 marks its two-phase form: the mask words of pairs up to `words`
+// 32-column words are kept in shared memory and SneakySnake runs as a
+// per-lane step loop over them (longer pairs take the fused loop).
 struct KernelCfg {
-    int tpp, dpt, ecap, xe;
+    int tpp, dpt, ecap, xe, words;
 };
 
 constexpr KernelCfg kBatchCfgs[] = {
@@ -25,7 +28,25 @@ constexpr KernelCfg kBatchCfgs[] = {
     {1, 6, 5, 5},    {1, 7, 6, 6},    {1, 8, 7, 7},    {1, 9, 8, 8},   {1, 10, 9, 9},
     {1, 11, 10, 10}, {1, 12, 11, 11}, {1, 13, 12, 12}, {1, 14, 13, 13}, {1, 15, 14, 14},
     {1, 16, 15, 15},
+    // two-phase forms, E = 1..12: as many words as keep a 4-warp block's
+    // arrays within about 56 KB (four blocks per SM)
+    {1, 2, 1, 1, 8},     {1, 3, 2, 2, 8},     {1, 4, 3, 3, 8},     {1, 5, 4, 4, 8},
+    {1, 6, 5, 5, 8},     {1, 7, 6, 6, 8},     {1, 8, 7, 7, 7},     {1, 9, 8, 8, 6},
+    {1, 10, 9, 9, 5},    {1, 11, 10, 10, 5},  {1, 12, 11, 11, 4},  {1, 13, 12, 12, 4},
 };
+
+// The two-phase form applies where SneakySnake runs (deciders 1 and 3);
+// GateKeeper alone runs a two-phase configuration as the fused loop.
+constexpr bool cfg_split(const KernelCfg &c, int dec) { return c.words > 0 && dec != 2; }
+// Block size and dynamic shared memory of a configuration's kernel.
+constexpr int cfg_threads(const KernelCfg &c, int dec) {
+    return cfg_split(c, dec) ? kSplitWarps * 32 : 256;
+}
+constexpr size_t cfg_smem(const KernelCfg &c, int dec) {
+    return cfg_split(c, dec)
+               ? (size_t)kSplitWarps * c.words * (2 * c.xe + 1) * 32 * sizeof(uint32_t)
+               : 0;
+}
 
 // a configuration serves threshold E
 constexpr bool cfg_serves(const KernelCfg &c, int E) {

@@ -244,7 +244,7 @@ def test_every_batched_configuration(pf, ctx):
         P = synth.generate(synth.SKEWED, 900 + E, 2500, m=150 if E < 20 else 250, E=E,
                            kmax=max(60, 3 * E))
         data[E] = (P, DevicePairs(ctx, P, fixed=int(P.lens[0])), oracle_filter(P, 3))
-    for ci, (tpp, dpt, ecap, xe) in enumerate(cfgs):
+    for ci, (tpp, dpt, ecap, xe, words) in enumerate(cfgs):
         for E, (P, D, (oa, oc)) in data.items():
             if xe >= 0 and E != xe:
                 continue
@@ -406,13 +406,33 @@ def test_filter_verify_path(pf, ctx, case_data, name):
     assert np.all(oa[0][vb <= P.E] == 1)
 
 
+def test_two_phase_configs_on_ragged_pairs(pf, ctx, case_data):
+    """The two-phase kernels on mixed lengths and thresholds: pairs longer
+    than their shared arrays take the fused loop in the same warps."""
+    from gpu_util import filter_dev
+    P, D, (oa, oc) = case_data["cfg3_mixed"]
+    cfgs = pf.pf_kernel_configs()
+    for dec in (1, 3):
+        for e in range(0, 21):
+            two = [i for i, c in enumerate(cfgs) if c[3] == e and c[4] > 0]
+            if two:
+                pf.pf_tune_set(ctx, dec, e, two[0], 64)
+            else:
+                pf.pf_tune_set(ctx, dec, e, next(i for i, c in enumerate(cfgs)
+                                                 if c[3] < 0 and c[2] >= e), 64)
+        a, c = filter_dev(ctx, D, dec)
+        want_c = oc if dec == 3 else oc[[0]]
+        want_a = oa if dec == 3 else oa[[0]]
+        assert np.array_equal(c, want_c) and np.array_equal(a, want_a)
+
+
 # ---- scheduler tuning ------------------------------------------------------------
 
 def test_tuner_picks_a_valid_config_and_stays_exact(pf, ctx, case_data):
     from gpu_util import filter_dev
     P, D, (oa, oc) = case_data["cfg2_150bp_E6"]
     cfg, chunk, ms = pf.pf_tune(ctx, 3, D.pairs, D.lens, 6, reps=1)
-    tpp, dpt, ecap, xe = pf.pf_kernel_configs()[cfg]
+    tpp, dpt, ecap, xe, words = pf.pf_kernel_configs()[cfg]
     assert (xe == 6 or (xe < 0 and ecap >= 6)) and ms > 0 and chunk in (64, 256, 1024)
     assert pf.pf_tune_get(ctx, 3, 6) == (cfg, chunk)
     a, c = filter_dev(ctx, D, 3)
