@@ -372,6 +372,8 @@ typedef struct {
     /* seconds summed over completed requests: waiting for admission,
      * uploading, on the device (published to complete), results back */
     double queue_s, stage_s, device_s, drain_s;
+    /* the longest single request in each of those phases, seconds */
+    double queue_max_s, stage_max_s, device_max_s, drain_max_s;
 } pf_serve_stats;
 
 /* Start serving on ctx (PF_EBUSY if already serving).  Allocates the

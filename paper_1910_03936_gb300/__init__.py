@@ -75,7 +75,9 @@ class ServeStats(ctypes.Structure):
                 ("failed", ctypes.c_uint64), ("pairs_completed", ctypes.c_uint64),
                 ("loop_launches", ctypes.c_uint64), ("queue_s", ctypes.c_double),
                 ("stage_s", ctypes.c_double), ("device_s", ctypes.c_double),
-                ("drain_s", ctypes.c_double)]
+                ("drain_s", ctypes.c_double), ("queue_max_s", ctypes.c_double),
+                ("stage_max_s", ctypes.c_double), ("device_max_s", ctypes.c_double),
+                ("drain_max_s", ctypes.c_double)]
 
 
 _lib = None

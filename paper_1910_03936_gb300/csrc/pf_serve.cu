@@ -541,10 +541,18 @@ void scheduler(ServeState *Sp) {
                 if (q->status == PF_OK) {
                     S.stats.completed++;
                     S.stats.pairs_completed += (uint64_t)q->req.n;
-                    S.stats.queue_s += secs(q->t_submit, q->t_admit);
-                    S.stats.stage_s += secs(q->t_admit, q->t_pub);
-                    S.stats.device_s += secs(q->t_pub, q->t_seen);
-                    S.stats.drain_s += secs(q->t_seen, q->t_done);
+                    const double tq = secs(q->t_submit, q->t_admit);
+                    const double ts = secs(q->t_admit, q->t_pub);
+                    const double td = secs(q->t_pub, q->t_seen);
+                    const double tr = secs(q->t_seen, q->t_done);
+                    S.stats.queue_s += tq;
+                    S.stats.stage_s += ts;
+                    S.stats.device_s += td;
+                    S.stats.drain_s += tr;
+                    S.stats.queue_max_s = std::max(S.stats.queue_max_s, tq);
+                    S.stats.stage_max_s = std::max(S.stats.stage_max_s, ts);
+                    S.stats.device_max_s = std::max(S.stats.device_max_s, td);
+                    S.stats.drain_max_s = std::max(S.stats.drain_max_s, tr);
                 } else {
                     S.stats.failed++;
                 }
