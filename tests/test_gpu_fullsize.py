@@ -76,14 +76,28 @@ def check_sample(P, acc, cnt, dist, seed):
 
 def test_headline_step_20M(pf, ctx):
     P = synth.generate(synth.SKEWED, 0x5EED0001, 20_000_000, m=150, E=6, kmax=60)
-    # the benchmark's kernel: exact-threshold E = 6, 64-pair work items
-    exact6 = [i for i, c in enumerate(pf.pf_kernel_configs()) if c[3] == 6][0]
+    # the benchmark's launch configuration: the autotuner's choice on the
+    # first 2M pairs, as the benchmark makes it
+    dev = "cuda:0"
+    reads = torch.from_numpy(P.reads[:2_000_000 * 150]).to(dev)
+    refs = torch.from_numpy(P.refs[:2_000_000 * 150]).to(dev)
+    sample = pf.pack_pairs(ctx, reads, refs, length=150)
+    lens = torch.full((2_000_000,), 150, dtype=torch.int32, device=dev)
     for dec in (1, 3):
-        pf.pf_tune_set(ctx, dec, 6, exact6, 64)
+        cfg, chunk, _ = pf.pf_tune(ctx, dec, sample, lens, 6, n=2_000_000, reps=2)
+        assert pf.pf_tune_get(ctx, dec, 6) == (cfg, chunk)
+    del reads, refs, sample, lens
     _, _, _, acc, cnt, dist = run_path(pf, ctx, P, fixed=150)
     check_sample(P, acc, cnt, dist, 1)
     # accept flags and distances agree with each other everywhere
     assert np.all((dist <= 6) <= (acc[0] == 1))
+    # and the fused and two-phase forms of the exact-E6 kernel give the same
+    # results on the whole batch
+    cfgs = pf.pf_kernel_configs()
+    for form in [i for i, c in enumerate(cfgs) if c[3] == 6]:
+        pf.pf_tune_set(ctx, 3, 6, form, 64)
+        _, _, _, a2, c2, d2 = run_path(pf, ctx, P, fixed=150)
+        assert np.array_equal(a2, acc) and np.array_equal(c2, cnt) and np.array_equal(d2, dist)
 
 
 def test_mixed_50M_device_and_host_pipeline(pf, ctx):
