@@ -1,4 +1,6 @@
 // Instantiates the filter kernels for one decider set PF_DEC (1, 2 or 3).
+#include <atomic>
+
 #include "pf_filter.cuh"
 #include "pf_kernels.h"
 
@@ -10,14 +12,24 @@ namespace pf {
 template <int I>
 using CfgAt = std::integral_constant<int, I>;
 
+// The two-phase kernels take more than the default 48 KB of dynamic shared
+// memory; the limit is raised once per device (a function attribute holds
+// per device).
+constexpr int kMaxDevices = 64;
+
 template <int I>
 static const void *batched_ptr_i() {
     constexpr KernelCfg c = kBatchCfgs[I];
     if constexpr (cfg_split(c, PF_DEC)) {
         const void *f = reinterpret_cast<const void *>(&filter_split_kernel<PF_DEC, c.xe, c.words>);
-        static const cudaError_t attr = cudaFuncSetAttribute(
-            f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg_smem(c, PF_DEC));
-        (void)attr;
+        static std::atomic<bool> raised[kMaxDevices];
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev >= 0 && dev < kMaxDevices && !raised[dev].load(std::memory_order_acquire)) {
+            if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)cfg_smem(c, PF_DEC)) == cudaSuccess)
+                raised[dev].store(true, std::memory_order_release);
+        }
         return f;
     } else {
         return reinterpret_cast<const void *>(&filter_batched_kernel<c.tpp, c.dpt, PF_DEC, c.xe>);
