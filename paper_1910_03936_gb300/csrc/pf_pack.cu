@@ -41,30 +41,45 @@ pack_ragged_kernel(const uint8_t *ascii, const int64_t *byte_off, const int64_t 
 }
 
 // Fixed layout: sequence s is ascii[s*len ...], words [s*W, (s+1)*W).
-// Block b packs global words [256 b, 256 b + 256); one 64-bit division per
-// block locates its first word, threads step from there.
+// Block b packs global words [512 b, 512 b + 512), two per thread (t and
+// t + 256, so each half is a coalesced run); both windows are loaded before
+// either is decoded.  One 64-bit division per block locates its first
+// word, threads step from there.
+constexpr int kPackWordsPerThread = 2;
+
 __global__ void __launch_bounds__(kPackThreads)
 pack_fixed_kernel(const uint8_t *ascii, int64_t nseq, int len, int W, uint32_t wmagic,
                   uint32_t *lo, uint32_t *hi, uint32_t *nm, unsigned *err) {
     __shared__ int64_t s_first;
     __shared__ int w_first;
     const int64_t total = nseq * (int64_t)W;
-    const int64_t gw0 = (int64_t)blockIdx.x * kPackThreads;
+    const int64_t gw0 = (int64_t)blockIdx.x * (kPackThreads * kPackWordsPerThread);
     if (threadIdx.x == 0) {
         s_first = gw0 / W;
         w_first = (int)(gw0 - s_first * W);
     }
     __syncthreads();
-    const int64_t gw = gw0 + threadIdx.x;
-    if (gw >= total) return;
-    const unsigned local = (unsigned)w_first + threadIdx.x;
-    // local / W by multiply-high when wmagic = ceil(2^32 / W) is exact for
-    // every local < W + 256 (W <= 4096), else by division
-    const unsigned q = wmagic ? __umulhi(local, wmagic) : local / (unsigned)W;
-    const int64_t s = s_first + q;
-    const int w = (int)(local - q * (unsigned)W);
-    pack_word(ascii + s * (int64_t)len, len, w, lo + gw, hi + gw, nm + gw, err,
-              ascii + nseq * (int64_t)len);
+    const uint8_t *lim = ascii + nseq * (int64_t)len;
+    PackWindow pw[kPackWordsPerThread];
+    int64_t gws[kPackWordsPerThread];
+#pragma unroll
+    for (int r = 0; r < kPackWordsPerThread; ++r) {
+        const unsigned local = (unsigned)w_first + threadIdx.x + (unsigned)(r * kPackThreads);
+        gws[r] = gw0 + threadIdx.x + r * kPackThreads;
+        if (gws[r] >= total) continue;
+        // local / W by multiply-high when wmagic = ceil(2^32 / W) is exact for
+        // every local < W + 512 (W <= 4096), else by division
+        const unsigned q = wmagic ? __umulhi(local, wmagic) : local / (unsigned)W;
+        const int64_t s = s_first + q;
+        const int w = (int)(local - q * (unsigned)W);
+        pack_load(ascii + s * (int64_t)len, len, w, lim, pw[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < kPackWordsPerThread; ++r) {
+        if (gws[r] >= total) continue;
+        const int64_t gw = gws[r];
+        pack_decode(pw[r], lo + gw, hi + gw, nm + gw, err);
+    }
 }
 
 }  // namespace
@@ -86,7 +101,8 @@ cudaError_t launch_pack_fixed(const uint8_t *ascii, int64_t nseq, int len, uint3
     const int64_t total = nseq * (int64_t)W;
     if (total <= 0) return cudaSuccess;
     (void)sms;
-    const int64_t blocks = (total + kPackThreads - 1) / kPackThreads;
+    const int64_t per_block = kPackThreads * kPackWordsPerThread;
+    const int64_t blocks = (total + per_block - 1) / per_block;
     const uint32_t wmagic =
         (W <= 4096) ? (uint32_t)((((uint64_t)1 << 32) + (uint64_t)W - 1) / (uint64_t)W) : 0u;
     pack_fixed_kernel<<<(unsigned)blocks, kPackThreads, 0, st>>>(ascii, nseq, len, W, wmagic,

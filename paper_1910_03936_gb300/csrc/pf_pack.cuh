@@ -80,7 +80,14 @@ __device__ __forceinline__ bool slow_word(const uint32_t *vals, int vb, uint32_t
     return found;
 }
 
-// Pack word w of a sequence whose bytes start at `src` (len bytes).  All 32
+// The 36 bytes that word w of a sequence needs, and where its bases start.
+struct PackWindow {
+    uint32_t u[9];  // aligned 4-byte words from the word's first base on
+    unsigned sh;    // bit offset of the first base in u[0]
+    int vb;         // valid bytes in the word, 1..32
+};
+
+// Load word w of a sequence whose bytes start at `src` (len bytes).  All 32
 // byte slots go through the fast path, including those past the end, which
 // are then forced to N.  `lim` is one past the last byte of the whole input
 // buffer: a word whose 36-byte window lies below it (rounded up to 4 bytes)
@@ -89,29 +96,32 @@ __device__ __forceinline__ bool slow_word(const uint32_t *vals, int vb, uint32_t
 // and count as "NNNN".  A byte past the end that is not a base only sends
 // the word to the exact path.
 template <typename L = LdNC>
-__device__ __forceinline__ void pack_word(const uint8_t *src, int len, int w, uint32_t *lo,
-                                          uint32_t *hi, uint32_t *nm, unsigned *err,
-                                          const uint8_t *lim) {
+__device__ __forceinline__ void pack_load(const uint8_t *src, int len, int w, const uint8_t *lim,
+                                          PackWindow &pw) {
     const int b0 = 32 * w;
-    const int vb = min(32, len - b0);  // valid bytes in this word, >= 1
+    pw.vb = min(32, len - b0);
     const uintptr_t a = reinterpret_cast<uintptr_t>(src + b0);
     const uint32_t *aw = reinterpret_cast<const uint32_t *>(a & ~uintptr_t(3));
-    const unsigned sh = 8u * unsigned(a & 3u);
-    uint32_t u[9];
+    pw.sh = 8u * unsigned(a & 3u);
     if (reinterpret_cast<uintptr_t>(aw + 9) <= ((reinterpret_cast<uintptr_t>(lim) + 3u) & ~uintptr_t(3))) {
 #pragma unroll
-        for (int k = 0; k < 9; ++k) u[k] = L::ld(aw + k);
+        for (int k = 0; k < 9; ++k) pw.u[k] = L::ld(aw + k);
     } else {
-        const uintptr_t end = a + (uintptr_t)vb;  // one past the last valid byte
+        const uintptr_t end = a + (uintptr_t)pw.vb;  // one past the last valid byte
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
             const uintptr_t wa = reinterpret_cast<uintptr_t>(aw + k);
-            u[k] = (wa < end) ? L::ld(aw + k) : 0x4e4e4e4eu;
+            pw.u[k] = (wa < end) ? L::ld(aw + k) : 0x4e4e4e4eu;
         }
     }
+}
+
+// The three plane words of a loaded window.
+__device__ __forceinline__ void pack_decode(const PackWindow &pw, uint32_t *lo, uint32_t *hi,
+                                            uint32_t *nm, unsigned *err) {
     uint32_t v[8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = __funnelshift_r(u[i], u[i + 1], sh);
+    for (int i = 0; i < 8; ++i) v[i] = __funnelshift_r(pw.u[i], pw.u[i + 1], pw.sh);
     uint32_t olo = 0u, ohi = 0u, onm = 0u, bad = 0u;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -124,14 +134,23 @@ __device__ __forceinline__ void pack_word(const uint8_t *src, int len, int w, ui
         onm |= (gather8<3>(y) >> (24 - 8 * i)) & keep;
     }
     if (bad) {
-        if (slow_word(v, vb, lo, hi, nm)) atomicOr(err, ERR_BYTES);
+        if (slow_word(v, pw.vb, lo, hi, nm)) atomicOr(err, ERR_BYTES);
         return;
     }
-    const uint32_t vmask = (vb >= 32) ? 0xffffffffu : ((1u << vb) - 1u);
+    const uint32_t vmask = (pw.vb >= 32) ? 0xffffffffu : ((1u << pw.vb) - 1u);
     onm |= ~vmask;      // bytes past the end are N
     *lo = olo & ~onm;   // N carries code 00
     *hi = ohi & ~onm;
     *nm = onm;
+}
+
+template <typename L = LdNC>
+__device__ __forceinline__ void pack_word(const uint8_t *src, int len, int w, uint32_t *lo,
+                                          uint32_t *hi, uint32_t *nm, unsigned *err,
+                                          const uint8_t *lim) {
+    PackWindow pw;
+    pack_load<L>(src, len, w, lim, pw);
+    pack_decode(pw, lo, hi, nm, err);
 }
 
 }  // namespace pf
