@@ -67,12 +67,18 @@ __device__ __forceinline__ U win(uint32_t x0, uint32_t x1, uint32_t x2, int t) {
 }
 
 // One DP column: reference base at bit t of the reference word f, band rows
-// read from the window at offset t.  VP keeps the bottom stand-in bit set;
-// bit 0 of the new top-row differences goes to the top of accP / accM.
+// read from the window at offset t.  VP keeps the bottom stand-in bit set.
+//
+// The column's horizontal differences would enter the next row up (shift
+// left, +1 entering above the top row) and the new vertical differences
+// would then move down one row with the band (shift right); the two shifts
+// cancel except on D0, so the new vectors come from D0 >> 1 directly.  The
+// top row's new vertical difference is then never +1 and is -1 exactly when
+// bit 0 of D0 is set: T grows by 1 per column, less the number of those
+// bits, which go to the top of accM.
 template <typename U>
 __device__ __forceinline__ void column(const ReadWin &r, const Word3 &f, int t, U store_mask,
-                                       U bottom, U &VP, U &VN, uint32_t &accP,
-                                       uint32_t &accM) {
+                                       U bottom, U &VP, U &VN, uint32_t &accM) {
     const U mlo = spread<U>(bcast(f.lo, t));
     const U mhi = spread<U>(bcast(f.hi, t));
     const U fn = spread<U>(bcast(f.nm, t));
@@ -83,19 +89,14 @@ __device__ __forceinline__ void column(const ReadWin &r, const Word3 &f, int t, 
     // Bits above the band (q > 2E) only ever influence higher bits (carries
     // and the left shifts run upwards), and the stored vectors drop them.
     const U Eq = ~((wlo ^ mlo) | (whi ^ mhi) | wnm | fn);
-    const U Pv = VP;
     const U X = Eq | VN;
-    const U D0 = (((X & Pv) + Pv) ^ Pv) | X;
-    U Ph = VN | ~(D0 | Pv);
-    U Mh = Pv & D0;
-    Ph = (Ph << 1) | U(1);  // +1 enters above the top row
-    Mh = Mh << 1;
-    const U nPv = Mh | ~(D0 | Ph);
-    const U nMv = Ph & D0;
-    accP = __funnelshift_r(accP, (uint32_t)nPv, 1);
-    accM = __funnelshift_r(accM, (uint32_t)nMv, 1);
-    VP = ((nPv >> 1) & store_mask) | bottom;
-    VN = (nMv >> 1) & store_mask;
+    const U D0 = (((X & VP) + VP) ^ VP) | X;
+    const U Ph = VN | ~(D0 | VP);
+    const U Mh = VP & D0;
+    const U D1 = D0 >> 1;
+    accM = __funnelshift_r(accM, (uint32_t)D0, 1);
+    VP = ((Mh | ~(D1 | Ph)) & store_mask) | bottom;
+    VN = Ph & D1 & store_mask;
 }
 
 template <typename U, typename L = LdNC>
@@ -138,18 +139,18 @@ __device__ __forceinline__ int verify_pair(const PairsView &pv, int64_t p, int m
             r.lo2 = r.hi2 = r.nm2 = 0u;
         }
         const int ncol = min(32, m - 32 * fw);
-        uint32_t accP = 0u, accM = 0u;
+        uint32_t accM = 0u;
         if (ncol == 32) {
 #pragma unroll
             for (int t = 0; t < 32; ++t)
-                column<U>(r, f, t, store_mask, bottom, VP, VN, accP, accM);
+                column<U>(r, f, t, store_mask, bottom, VP, VN, accM);
         } else {
             for (int t = 0; t < ncol; ++t)
-                column<U>(r, f, t, store_mask, bottom, VP, VN, accP, accM);
+                column<U>(r, f, t, store_mask, bottom, VP, VN, accM);
         }
         // top cell D(j-E, j) after the word: each column adds 1 + its top
-        // row's new difference
-        T += ncol + __popc(accP) - __popc(accM);
+        // row's new difference (0 or -1)
+        T += ncol - __popc(accM);
         // Early exit: the band's smallest value is at least T minus the
         // number of -1 differences.  Past E, every path through this column
         // costs more than E, so the distance saturates (the values that the
