@@ -478,39 +478,32 @@ __device__ __forceinline__ int split_sneakysnake(const uint32_t *mine, int W, ui
 #pragma unroll
     for (int k = 0; k < NS; ++k) Mw[k] = mine[k * 32];
     int ws = 0, kss = 0;
-    uint32_t C = 0xffffffffu, dead = 0u;
-    bool cont = false;
+    uint32_t C = 0xffffffffu;
+    // One step shape for every lane: a pipe that runs on from the previous
+    // word is the word's first step with every column open, and the
+    // diagonals already blocked carry bit 0 set (blocked at once), which no
+    // later step of the word looks at (they start past the first obstacle).
     for (;;) {
         uint32_t T = 0xffffffffu;
-        if (cont) {  // a pipe runs on from the previous word
 #pragma unroll
-            for (int k = 0; k < NS; ++k) {
-                const uint32_t y = Mw[k] | ((dead >> k) & 1u);
-                T &= y | (y * neg1);
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < NS; ++k) {
-                const uint32_t y = Mw[k] & C;
-                T &= y | (y * neg1);
-            }
+        for (int k = 0; k < NS; ++k) {
+            const uint32_t y = Mw[k] & C;
+            T &= y | (y * neg1);
         }
         if (T == 0u) {  // the deepest pipe reaches the end of the word
             if (ws == W - 1) break;
-            uint32_t dd = cont ? dead : 0u;
+            uint32_t dead = 0u;
 #pragma unroll
             for (int k = 0; k < NS; ++k)
-                if (Mw[k] & (cont ? 0xffffffffu : C)) dd |= 1u << k;
-            dead = dd;
-            cont = true;
+                if (Mw[k] & C) dead |= 1u << k;
             ++ws;
 #pragma unroll
-            for (int k = 0; k < NS; ++k) Mw[k] = mine[(ws * NS + k) * 32];
+            for (int k = 0; k < NS; ++k) Mw[k] = mine[(ws * NS + k) * 32] | ((dead >> k) & 1u);
+            C = 0xffffffffu;
             continue;
         }
         const int pbit = __ffs(T) - 1;
         ++kss;
-        cont = false;
         if (kss > XE) break;
         if (pbit == 31) {  // the obstacle was the word's last column
             if (ws == W - 1) break;
