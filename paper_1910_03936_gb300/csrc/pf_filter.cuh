@@ -492,13 +492,10 @@ __device__ __forceinline__ int split_sneakysnake(const uint32_t *mine, int W, ui
         }
         if (T == 0u) {  // the deepest pipe reaches the end of the word
             if (ws == W - 1) break;
-            uint32_t dead = 0u;
-#pragma unroll
-            for (int k = 0; k < NS; ++k)
-                if (Mw[k] & C) dead |= 1u << k;
             ++ws;
 #pragma unroll
-            for (int k = 0; k < NS; ++k) Mw[k] = mine[(ws * NS + k) * 32] | ((dead >> k) & 1u);
+            for (int k = 0; k < NS; ++k)  // blocked in the rest of this word: blocked at once
+                Mw[k] = mine[(ws * NS + k) * 32] | ((Mw[k] & C) ? 1u : 0u);
             C = 0xffffffffu;
             continue;
         }
