@@ -409,14 +409,25 @@ def main_gpu(args):
         return
     if args.stage != "step":
         dec = args.deciders
-        fn = pf.pf_filter_plain if args.stage == "filter_plain" else pf.pf_filter
         # one threshold for every pair: no per-pair E array, one kernel launch
+        if args.stage in ("filter_plain", "filter_batched"):
+            f0 = pf.pf_filter_plain if args.stage == "filter_plain" else pf.pf_filter
+            fn = lambda: f0(ctx, dec, pairs, lens, None, E_HEAD, acc, cnt, n)
+        elif args.stage == "partitioned":
+            fn = lambda: pf.pf_filter_partitioned(ctx, pairs, lens, None, E_HEAD, 8, 2, acc[:n],
+                                                  cnt[:n], n)
+        elif args.stage == "shouji":
+            fn = lambda: pf.pf_filter_shouji(ctx, pairs, lens, None, E_HEAD, acc[:n], cnt[:n], n)
+        else:  # shd
+            fn = lambda: pf.pf_filter_shd(ctx, pairs, lens, None, E_HEAD,
+                                          pf.PF_SHD_VACANT_ZERO | pf.PF_SHD_STREAK, acc[:n],
+                                          cnt[:n], n)
         for _ in range(args.warmup):
-            fn(ctx, dec, pairs, lens, None, E_HEAD, acc, cnt, n)
+            fn()
         a0, a1 = ev(), ev()
         a0.record(stream)
         for _ in range(args.steps):
-            fn(ctx, dec, pairs, lens, None, E_HEAD, acc, cnt, n)
+            fn()
         a1.record(stream)
         torch.cuda.synchronize(dev)
         fms = a0.elapsed_time(a1) / args.steps
@@ -549,9 +560,9 @@ def main_gpu(args):
     # (profiles/), scaled to this launch by the units processed; valid for
     # the kernels as captured (the two-phase exact-E6 filter the tuner picks,
     # pack_fixed, verify<u32>)
-    traffic_per_pair = {"filter": (248.083456e6 + 10.464e6) / 2e6,
-                        "pack": 2 * (300.0896e6 + 95.116544e6) / 4e6,
-                        "verify": (224.882944e6 + 6.427648e6) / 2e6}
+    traffic_per_pair = {"filter": (248.083456e6 + 10.268928e6) / 2e6,
+                        "pack": 2 * (300.065024e6 + 94.899712e6) / 4e6,
+                        "verify": (223.07456e6 + 6.509312e6) / 2e6}
     sm_mhz = clk.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
     alu_peak = 152 * 64 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # Top/s, ALU pipe
     ms_dom = stages[dominant]
@@ -638,7 +649,9 @@ def main():
                     help="time the step only (for profiling): no side measurements")
     ap.add_argument("--cfg", type=int, default=None, help="force batch kernel configuration")
     ap.add_argument("--chunk", type=int, default=64)
-    ap.add_argument("--stage", default="step", choices=["step", "filter_plain", "filter_batched", "serve"],
+    ap.add_argument("--stage", default="step",
+                    choices=["step", "filter_plain", "filter_batched", "serve", "partitioned",
+                             "shouji", "shd"],
                     help="time one filter kernel instead of the step (profiling)")
     ap.add_argument("--deciders", type=int, default=3)
     ap.add_argument("--no-serve", action="store_true")
