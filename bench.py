@@ -284,14 +284,10 @@ def run_other_workload(args):
         step = lambda: (pack(), pf.pf_filter(ctx, 1, pairs, lens, E, 5, acc, cnt, n))
         out["step"] = "pack + batched SneakySnake"
     else:
-        # one threshold: tune it on a sample of the batch; several (the mixed
-        # batch): keep the defaults, since a sample of the whole batch at one
-        # threshold does not represent that threshold's bin (its lengths)
-        tuned_w = {}
-        if len(np.unique(P.E)) == 1:
-            e = int(P.E[0])
-            tuned_w[e] = pf.pf_tune(ctx, 3, pairs, lens, e, n=min(n, 1_000_000), reps=1)[:2]
-        out["tuned_cfg"] = tuned_w
+        # the autotuner on the batch as it is: each threshold timed on up to
+        # 1M of its own pairs
+        pf.pf_tune_batch(ctx, 3, pairs, lens, E, Emax, n=n, sample=1 << 20, reps=1)
+        out["tuned_cfg"] = {int(e): pf.pf_tune_get(ctx, 3, int(e)) for e in np.unique(P.E)}
         out["filter_ms"] = timed(lambda: pf.pf_filter(ctx, 3, pairs, lens, E, Emax, acc, cnt, n), reps)
         out["filter_verify_ms"] = timed(
             lambda: pf.pf_filter_verify(ctx, 3, pairs, lens, E, Emax, acc, cnt, dist, n), reps)

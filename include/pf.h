@@ -190,6 +190,19 @@ PF_API pf_status pf_filter_plain(pf_ctx *ctx, unsigned deciders, const pf_pairs 
 PF_API pf_status pf_kernel_configs(int *tpp, int *dpt, int *ecap, int *exact_e, int *words,
                                    int cap, int *count);
 
+/* Autotune on a batch as it is: its pairs are grouped by threshold (E,
+ * device int16[n], required), and for every threshold with at least 1,024
+ * pairs each configuration serving it (and work items of 64, 256 and 1,024
+ * pairs) is timed on up to `sample` of that threshold's own pairs (0 =
+ * 2^20), reps timed runs each after one warm-up; the fastest becomes the
+ * scheduler's choice for (deciders, E).  Thresholds with fewer pairs keep
+ * their choice.  Synchronises the context stream; allocates its output
+ * buffers (freed on return).  PF_EINVAL as pf_filter, or for n <= 0,
+ * reps <= 0, sample < 0 or a NULL E. */
+PF_API pf_status pf_tune_batch(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs,
+                               const int32_t *lens, const int16_t *E, int E_max, int64_t n,
+                               int64_t sample, int reps);
+
 /* Batches of fewer than `pairs` pairs skip the scheduler: one launch of the
  * plain one-thread-per-pair kernel serving E_max, no binning and no
  * per-threshold launches, whose fixed costs dominate small batches.

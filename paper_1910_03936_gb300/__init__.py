@@ -23,7 +23,7 @@ __all__ = [
     "ServeConfig", "Request", "pf_serve_start", "pf_submit", "pf_poll", "pf_wait",
     "pf_serve_resume", "pf_serve_stats_get", "pf_serve_stop", "pf_serve_replay", "pf_run_host",
     "pf_filter_partitioned", "pf_filter_shouji", "pf_filter_shd", "PF_SHD_VACANT_ZERO",
-    "PF_SHD_STREAK", "pf_set_small_batch",
+    "PF_SHD_STREAK", "pf_set_small_batch", "pf_tune_batch",
 ]
 
 PF_SNEAKYSNAKE = 1
@@ -127,6 +127,7 @@ def load():
         "pf_serve_replay": [P, P, I, P, I, P, ctypes.POINTER(ctypes.c_double)],
         "pf_tune_set": [P, U, I, I, I],
         "pf_set_small_batch": [P, I64],
+        "pf_tune_batch": [P, U, ctypes.POINTER(_Pairs), P, P, I, I64, I64, I],
         "pf_tune_get": [P, U, I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
         "pf_tune": [P, U, ctypes.POINTER(_Pairs), P, I, I64, I, ctypes.POINTER(ctypes.c_int),
                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)],
@@ -421,6 +422,17 @@ def pf_kernel_configs():
 
 def pf_tune_set(ctx, deciders, E, cfg, chunk):
     _check(load().pf_tune_set(ctx.handle, int(deciders), int(E), int(cfg), int(chunk)), ctx.handle)
+
+
+def pf_tune_batch(ctx, deciders, pairs, lens, E, E_max, n=None, sample=0, reps=2):
+    """Autotune every threshold of this batch on its own pairs."""
+    _dt(lens, torch.int32, "lens")
+    _dt(E, torch.int16, "E")
+    n = lens.numel() if n is None else n
+    _cur_stream(ctx)
+    cp = pairs._c()
+    _check(load().pf_tune_batch(ctx.handle, int(deciders), ctypes.byref(cp), _p(lens), _p(E),
+                                int(E_max), int(n), int(sample), int(reps)), ctx.handle)
 
 
 def pf_set_small_batch(ctx, pairs):

@@ -580,6 +580,108 @@ pf_status pf_kernel_configs(int *tpp, int *dpt, int *ecap, int *exact_e, int *wo
     return PF_OK;
 }
 
+pf_status pf_tune_batch(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs,
+                        const int32_t *lens, const int16_t *E, int E_max, int64_t n,
+                        int64_t sample, int reps) {
+    if (!ctx) return PF_EINVAL;
+    if (n <= 0 || reps <= 0 || sample < 0 || !E)
+        return ctx->fail(PF_EINVAL, "pf_tune_batch: bad n/reps/sample or no per-pair E");
+    pf_status st = check_filter_args(ctx, deciders, pairs, lens, E_max,
+                                     reinterpret_cast<uint8_t *>(1),
+                                     reinterpret_cast<int16_t *>(2), n);
+    if (st != PF_OK) return st;
+    if (sample == 0) sample = int64_t(1) << 20;
+    cudaSetDevice(ctx->device);
+    Scratch s;
+    st = ctx->scratch_layout(n, &s);
+    if (st != PF_OK) return st;
+    // group the pairs by threshold: bin e holds the pairs with E = e
+    BinTable t;
+    for (int e = 0; e <= PF_MAX_E; ++e) t.cfg_of_E[e] = e;
+    const int64_t hb = std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)ctx->sms * 8));
+    bin_init_kernel<<<1, 32, 0, ctx->stream>>>(s.bin_start, s.work, s.hist, kNumBatchCfgs, -1, n);
+    bin_hist_kernel<<<(unsigned)hb, 256, 0, ctx->stream>>>(E, n, E_max, t, s.hist);
+    bin_scan_kernel<<<1, 32, 0, ctx->stream>>>(s.hist, s.bin_start, s.cursor, s.ident);
+    bin_scatter_kernel<<<(unsigned)hb, 256, 0, ctx->stream>>>(E, n, E_max, t, s.cursor, s.order,
+                                                               s.ident);
+    int64_t starts[PF_MAX_E + 2];
+    st = ctx->cuda(cudaMemcpyAsync(starts, s.bin_start, sizeof(starts), cudaMemcpyDeviceToHost,
+                                   ctx->stream),
+                   "pf_tune_batch bins");
+    if (st == PF_OK) st = ctx->cuda(cudaStreamSynchronize(ctx->stream), "pf_tune_batch sync");
+    if (st != PF_OK) return st;
+    const int slots = (deciders == 3u) ? 2 : 1;
+    uint8_t *acc = nullptr;
+    int16_t *cnt = nullptr;
+    int64_t *range = nullptr;  // [2] positions timed, then the work counter
+    if (cudaMalloc(&acc, (size_t)slots * n) != cudaSuccess ||
+        cudaMalloc(&cnt, (size_t)slots * n * sizeof(int16_t)) != cudaSuccess ||
+        cudaMalloc(&range, 4 * sizeof(int64_t)) != cudaSuccess) {
+        cudaGetLastError();
+        if (acc) cudaFree(acc);
+        if (cnt) cudaFree(cnt);
+        return ctx->fail(PF_ENOMEM, "pf_tune_batch: buffers");
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    static const int chunks[] = {64, 256, 1024};
+    for (int e = 0; e <= E_max && st == PF_OK; ++e) {
+        const int64_t lo = starts[e], hi = std::min(starts[e + 1], starts[e] + sample);
+        if (hi - lo < 1024) continue;  // too few pairs at this threshold to time
+        int64_t r[2] = {lo, hi};
+        cudaMemcpy(range, r, sizeof(r), cudaMemcpyHostToDevice);
+        BatchArgs b;
+        b.f = make_filter_args(ctx, pairs, lens, E, E_max, acc, cnt, n);
+        b.order = s.order;
+        b.bin_start = range;
+        b.bin_cfg = nullptr;
+        b.nbins = 1;
+        b.work = reinterpret_cast<unsigned long long *>(range + 2);
+        b.chunk_start = nullptr;
+        b.ident = s.ident;
+        int bc = ctx->tune_cfg[deciders][e], bk = ctx->tune_chunk[deciders][e];
+        float bms = 1e30f;
+        for (int c = 0; st == PF_OK && c < kNumBatchCfgs; ++c) {
+            if (!cfg_serves(kBatchCfgs[c], e)) continue;
+            for (int k : chunks) {
+                b.chunk = k;
+                const int wpb = cfg_threads(kBatchCfgs[c], (int)deciders) / 32;
+                const int64_t items = (hi - lo + k - 1) / k;
+                const int grid = (int)std::min<int64_t>(ctx->grid_for((int)deciders, c),
+                                                        std::max<int64_t>(1, (items + wpb - 1) / wpb));
+                float best = 1e30f;
+                for (int rep = 0; rep <= reps && st == PF_OK; ++rep) {  // the first run warms up
+                    cudaMemsetAsync(b.work, 0, sizeof(unsigned long long), ctx->stream);
+                    cudaEventRecord(e0, ctx->stream);
+                    st = ctx->cuda(launch_filter_batched((int)deciders, c, grid, b, 0, ctx->stream),
+                                   "pf_tune_batch launch");
+                    cudaEventRecord(e1, ctx->stream);
+                    if (st == PF_OK) st = ctx->cuda(cudaEventSynchronize(e1), "pf_tune_batch sync");
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (rep > 0 && ms < best) best = ms;
+                }
+                if (best < bms) {
+                    bms = best;
+                    bc = c;
+                    bk = k;
+                }
+            }
+        }
+        if (st == PF_OK) {
+            ctx->tune_cfg[deciders][e] = bc;
+            ctx->tune_chunk[deciders][e] = bk;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(acc);
+    cudaFree(cnt);
+    cudaFree(range);
+    return st;
+}
+
 pf_status pf_set_small_batch(pf_ctx *ctx, int64_t pairs) {
     if (!ctx) return PF_EINVAL;
     if (pairs < 0) return ctx->fail(PF_EINVAL, "pf_set_small_batch: pairs < 0");

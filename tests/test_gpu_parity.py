@@ -439,6 +439,21 @@ def test_tuner_picks_a_valid_config_and_stays_exact(pf, ctx, case_data):
     assert np.array_equal(c, oc) and np.array_equal(a, oa)
 
 
+def test_tune_batch_tunes_each_threshold_on_its_own_pairs(pf, ctx, case_data):
+    from gpu_util import filter_dev
+    P, D, (oa, oc) = case_data["cfg3_mixed"]
+    cfgs = pf.pf_kernel_configs()
+    pf.pf_tune_batch(ctx, 3, D.pairs, D.lens, D.E, D.E_max, reps=1)
+    for e, count in zip(*np.unique(P.E, return_counts=True)):
+        cfg, chunk = pf.pf_tune_get(ctx, 3, int(e))
+        tpp, dpt, ecap, xe, words = cfgs[cfg]
+        assert (xe == e or (xe < 0 and ecap >= e)) and chunk in (64, 256, 1024)
+    a, c = filter_dev(ctx, D, 3)
+    assert np.array_equal(c, oc) and np.array_equal(a, oa)
+    with pytest.raises(pf.PFError):
+        pf.pf_tune_batch(ctx, 3, D.pairs, D.lens, D.E, D.E_max, reps=0)
+
+
 def test_small_batches_take_one_plain_launch(pf, case_data):
     """With the default small-batch rule, pf_filter and pf_filter_verify on
     small batches run the plain kernel; results are the same."""
