@@ -190,10 +190,10 @@ int pf_ctx::grid_for(int dec, int cfg) {
 
 // Default configuration for threshold E before any tuning: the
 // exact-threshold one-thread kernel up to E = 15 (its two-phase form for
-// E = 3..7, whose shared arrays hold pairs up to 256 bases), eight lanes
-// per pair above.
+// E = 1..7, with shared arrays that hold pairs up to 256 bases), eight
+// lanes per pair above.
 int pf::pf_default_cfg(int E) {
-    if (E >= 3 && E <= 7)
+    if (E >= 1 && E <= 7)
         for (int c = 0; c < kNumBatchCfgs; ++c)
             if (kBatchCfgs[c].xe == E && kBatchCfgs[c].words >= 8) return c;
     if (E <= 15) return kFirstExactCfg + E;
