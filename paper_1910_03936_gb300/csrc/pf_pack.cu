@@ -1,5 +1,8 @@
-// a1: pack kernels.  One thread builds one 32-bit word of each plane from
-// 32 bytes (device functions in pf_pack.cuh).
+// a1: pack kernels.  The fixed layout decodes the buffer as a stream of
+// aligned 32-byte chunks and cuts the sequences' words out of it; the
+// ragged layout (and sequences longer than 4096 words) builds each 32-bit
+// word of each plane from the 32 bytes of its own window (device functions
+// in pf_pack.cuh).
 #include "pf_pack.cuh"
 
 namespace pf {
@@ -82,6 +85,120 @@ pack_fixed_kernel(const uint8_t *ascii, int64_t nseq, int len, int W, uint32_t w
     }
 }
 
+// Stream-tiled fixed layout.  Chunk j of the buffer is its 32 bytes from
+// A + 32 j, A = the buffer start rounded down to 32 bytes; decoded, it is
+// one word per plane whose bit b is byte A + 32 j + b.  Word w of sequence
+// s is the 32 bits of that stream from byte s*len + 32 w, one funnel shift
+// per plane over two chunk words.  A block packs kStreamWords consecutive
+// words (s-major): their start bytes rise by at most 32 from one word to
+// the next, so they span at most kStreamWords + 1 chunks, which the block
+// decodes into shared memory first (two 16-byte loads per chunk, no
+// re-reads), then cuts out its words.
+constexpr int kStreamWords = 1023;
+constexpr int kStreamChunksPerThread = (kStreamWords + 1) / kPackThreads;
+static_assert(kStreamChunksPerThread * kPackThreads == kStreamWords + 1, "chunk split");
+
+__global__ void __launch_bounds__(kPackThreads, 4)
+pack_stream_kernel(const uint8_t *ascii, int64_t nseq, int len, int W, uint32_t wmagic,
+                   uint32_t *lo, uint32_t *hi, uint32_t *nm, unsigned *err) {
+    __shared__ uint4 chunk[kStreamWords + 1];
+    __shared__ int64_t s_j0;
+    __shared__ int s_wfirst, s_nchunks, s_base;
+    const int64_t total = nseq * (int64_t)W;
+    const int64_t g0 = (int64_t)blockIdx.x * kStreamWords;
+    const uintptr_t src = reinterpret_cast<uintptr_t>(ascii);
+    const uintptr_t A = src & ~uintptr_t(31);
+    const int delta = (int)(src - A);
+    if (threadIdx.x == 0) {
+        const int64_t sf = g0 / W;
+        const int wf = (int)(g0 - sf * W);
+        const int64_t g1 = min(g0 + kStreamWords, total) - 1;
+        const int64_t sl = g1 / W;
+        const int64_t pf = sf * len + 32 * wf + delta;  // bytes from A
+        const int64_t pl = sl * len + 32 * (g1 - sl * W) + delta;
+        s_j0 = pf >> 5;
+        s_wfirst = wf;
+        s_nchunks = (int)((pl >> 5) + 2 - (pf >> 5));
+        s_base = (int)((pf & 31) - 32 * wf);  // s_first*len + delta - 32*j0
+    }
+    __syncthreads();
+    const int nchunks = s_nchunks;
+    const uintptr_t cbase = A + 32 * (uintptr_t)s_j0;
+    // bytes of the buffer, and the 4-byte words that hold them
+    const uintptr_t vbeg = src, vend = src + (uintptr_t)(nseq * (int64_t)len);
+    const uintptr_t lo4 = vbeg & ~uintptr_t(3), hi4 = (vend + 3) & ~uintptr_t(3);
+
+    uint32_t v[kStreamChunksPerThread][8];
+#pragma unroll
+    for (int r = 0; r < kStreamChunksPerThread; ++r) {
+        const int c = threadIdx.x + r * kPackThreads;
+        if (c >= nchunks) continue;
+        const uintptr_t ca = cbase + 32 * (uintptr_t)c;
+        if (ca >= lo4 && ca + 32 <= hi4) {
+            const uint4 x0 = __ldg(reinterpret_cast<const uint4 *>(ca));
+            const uint4 x1 = __ldg(reinterpret_cast<const uint4 *>(ca + 16));
+            v[r][0] = x0.x; v[r][1] = x0.y; v[r][2] = x0.z; v[r][3] = x0.w;
+            v[r][4] = x1.x; v[r][5] = x1.y; v[r][6] = x1.z; v[r][7] = x1.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const uintptr_t wa = ca + 4 * k;
+                v[r][k] = (wa >= lo4 && wa < hi4) ? __ldg(reinterpret_cast<const uint32_t *>(wa))
+                                                  : 0x4e4e4e4eu;
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < kStreamChunksPerThread; ++r) {
+        const int c = threadIdx.x + r * kPackThreads;
+        if (c >= nchunks) continue;
+        uint32_t l, h, n;
+        if (decode32(v[r], l, h, n)) {
+            const uintptr_t ca = cbase + 32 * (uintptr_t)c;
+            const int vlo = (vbeg > ca) ? (int)(vbeg - ca) : 0;
+            const int vhi = (vend < ca + 32) ? (int)((intptr_t)vend - (intptr_t)ca) : 32;
+            const uint4 e = slow_chunk(make_uint4(v[r][0], v[r][1], v[r][2], v[r][3]),
+                                       make_uint4(v[r][4], v[r][5], v[r][6], v[r][7]), vlo, vhi);
+            if (e.w) atomicOr(err, ERR_BYTES);
+            l = e.x;
+            h = e.y;
+            n = e.z;
+        }
+        chunk[c] = make_uint4(l, h, n, 0u);
+    }
+    __syncthreads();
+
+#pragma unroll
+    for (int r = 0; r < kStreamChunksPerThread; ++r) {
+        const int i = threadIdx.x + r * kPackThreads;
+        const int64_t g = g0 + i;
+        if (i >= kStreamWords || g >= total) continue;
+        // (w_first + i) / W by multiply-high: with wmagic = ceil(2^32 / W) and
+        // 2 <= W <= 4096 the quotient is exact for every numerator below 2^20
+        // (ceil(2^32 / 1) does not fit 32 bits: W = 1 divides by itself)
+        const unsigned local = (unsigned)s_wfirst + (unsigned)i;
+        const unsigned q = (W == 1) ? local : __umulhi(local, wmagic);
+        const int w = (int)(local - q * (unsigned)W);
+        const int P = (int)q * len + 32 * w + s_base;  // byte of the word from chunk 0
+        const int j = P >> 5;
+        const unsigned sh = (unsigned)P & 31u;
+        const uint4 x = chunk[j], y = chunk[j + 1];
+        uint32_t l = __funnelshift_r(x.x, y.x, sh);
+        uint32_t h = __funnelshift_r(x.y, y.y, sh);
+        uint32_t n = __funnelshift_r(x.z, y.z, sh);
+        const int vb = len - 32 * w;
+        if (vb < 32) {  // bytes past the end of the sequence are N
+            const uint32_t m = (1u << vb) - 1u;
+            l &= m;
+            h &= m;
+            n |= ~m;
+        }
+        lo[g] = l;
+        hi[g] = h;
+        nm[g] = n;
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_pack_ragged(const uint8_t *ascii, const int64_t *byte_off,
@@ -101,12 +218,18 @@ cudaError_t launch_pack_fixed(const uint8_t *ascii, int64_t nseq, int len, uint3
     const int64_t total = nseq * (int64_t)W;
     if (total <= 0) return cudaSuccess;
     (void)sms;
+    if (W <= 4096) {
+        const int64_t blocks = (total + kStreamWords - 1) / kStreamWords;
+        const uint32_t wmagic =
+            (W == 1) ? 0u : (uint32_t)((((uint64_t)1 << 32) + (uint64_t)W - 1) / (uint64_t)W);
+        pack_stream_kernel<<<(unsigned)blocks, kPackThreads, 0, st>>>(ascii, nseq, len, W, wmagic,
+                                                                     lo, hi, nm, err);
+        return cudaGetLastError();
+    }
     const int64_t per_block = kPackThreads * kPackWordsPerThread;
     const int64_t blocks = (total + per_block - 1) / per_block;
-    const uint32_t wmagic =
-        (W <= 4096) ? (uint32_t)((((uint64_t)1 << 32) + (uint64_t)W - 1) / (uint64_t)W) : 0u;
-    pack_fixed_kernel<<<(unsigned)blocks, kPackThreads, 0, st>>>(ascii, nseq, len, W, wmagic,
-                                                                lo, hi, nm, err);
+    pack_fixed_kernel<<<(unsigned)blocks, kPackThreads, 0, st>>>(ascii, nseq, len, W, 0u, lo, hi,
+                                                                nm, err);
     return cudaGetLastError();
 }
 

@@ -9,7 +9,7 @@
 namespace pf {
 
 // Code bits of an ASCII base sit in bits 1..3 and ignore case:
-//   a/A 0x61/0x41 -> 000, c 0x63 -> 001, t 0x74 -> 010, g 0x67 -> 011,
+//   a/A 0x61/0x41 -> 000, c 0x63 -> 100, g 0x67 -> 110, t 0x74 -> 010,
 //   n 0x6e -> 111 (bit 1, bit 2, bit 3).
 // low code bit = bit1 ^ bit2, high code bit = bit2, N = bit3.
 //
@@ -30,17 +30,19 @@ __device__ __forceinline__ uint32_t gather8(uint32_t y) {
     return (y & (0x11111111u << S)) * (0x01020408u >> S);
 }
 
-// Canonical lower-case letter per 3-bit pattern (bits 1..3 of the byte),
-// as an 8-byte table for byte_perm: patterns 0,1,2,3,7 -> a,c,t,g,n;
-// 4,5,6 -> 0, which no lower-cased byte equals.
-constexpr uint32_t kCanonLo = 0x67746361u;  // g t c a
-constexpr uint32_t kCanonHi = 0x6e000000u;  // n . . .
+// Canonical lower-case letter per 3-bit pattern of bits 0..2, as an 8-byte
+// table for byte_perm: patterns 1,3,4,6,7 -> a,c,t,n,g (the five letters
+// differ there); 0,2,5 -> 0, which no lower-cased byte equals.  A byte is
+// a base or N exactly when, lower-cased, it equals the entry of its own
+// pattern.
+constexpr uint32_t kCanonLo = 0x63006100u;  // c . a .
+constexpr uint32_t kCanonHi = 0x676e0074u;  // g n . t
 
 // Nonzero iff one of the 8 bytes of (a, b) is not A/C/G/T/N (either case).
-// The patterns of Y, one per nibble, select the canonical letters of bytes
-// (a0 b0 a1 b1) and (a2 b2 a3 b3); the bytes are interleaved the same way.
+// The nibbles of Y select the canonical letters of bytes (a0 b0 a1 b1) and
+// (a2 b2 a3 b3); the bytes are interleaved the same way.
 __device__ __forceinline__ uint32_t invalid8(uint32_t a, uint32_t b, uint32_t y) {
-    const uint32_t z = (y >> 1) & 0x77777777u;
+    const uint32_t z = y & 0x77777777u;
     const uint32_t c0 = __byte_perm(kCanonLo, kCanonHi, z);
     const uint32_t c1 = __byte_perm(kCanonLo, kCanonHi, z >> 16);
     const uint32_t i0 = __byte_perm(a, b, 0x5140u);
@@ -48,25 +50,53 @@ __device__ __forceinline__ uint32_t invalid8(uint32_t a, uint32_t b, uint32_t y)
     return (c0 ^ (i0 | 0x20202020u)) | (c1 ^ (i1 | 0x20202020u));
 }
 
-// Per-byte exact classification of the first vb bytes, for words in which
-// the fast test saw a byte outside A/C/G/T/N.  Returns whether such a byte
-// lies among the first vb (bytes past vb are N and never an error).
-__device__ __forceinline__ bool slow_word(const uint32_t *vals, int vb, uint32_t *lo,
-                                          uint32_t *hi, uint32_t *nm) {
-    uint32_t olo = 0u, ohi = 0u, onm = 0u;
-    bool found = false;
+// Bits 24..31 of g0..g3 (the flags of bytes 0..7, 8..15, 16..23, 24..31)
+// as one word.
+__device__ __forceinline__ uint32_t join4(uint32_t g0, uint32_t g1, uint32_t g2, uint32_t g3) {
+    return __byte_perm(__byte_perm(g0, g1, 0x0073u), __byte_perm(g2, g3, 0x0073u), 0x5410u);
+}
+
+// The three plane words of 32 bytes (byte b in byte b%4 of v[b/4]), N
+// carrying code 00.  Returns nonzero if a byte is not A/C/G/T/N; the words
+// are then not meaningful.
+__device__ __forceinline__ uint32_t decode32(const uint32_t *v, uint32_t &lo, uint32_t &hi,
+                                             uint32_t &nm) {
+    uint32_t g1[4], g2[4], g3[4], bad = 0u;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const uint32_t y = interleave_nibbles(v[2 * i], v[2 * i + 1]);
+        bad |= invalid8(v[2 * i], v[2 * i + 1], y);
+        g1[i] = gather8<1>(y);
+        g2[i] = gather8<2>(y);
+        g3[i] = gather8<3>(y);
+    }
+    const uint32_t h = join4(g2[0], g2[1], g2[2], g2[3]);
+    nm = join4(g3[0], g3[1], g3[2], g3[3]);
+    lo = join4(g1[0], g1[1], g1[2], g1[3]) ^ h;  // N: bit1 = bit2 = 1 -> 0
+    hi = h & ~nm;
+    return bad;
+}
+
+// Per-byte exact classification of 32 bytes (bytes 0..15 in x, 16..31 in
+// y), for chunks in which the fast test saw a byte outside A/C/G/T/N.
+// Bytes outside [vlo, vhi) are N and never an error.  Returns the lo, hi
+// and N words and, in w, whether a byte inside is neither a base nor N
+// (such a byte packs as N).
+static __device__ __noinline__ uint4 slow_chunk(uint4 x, uint4 y, int vlo, int vhi) {
+    const uint32_t vals[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
+    uint32_t olo = 0u, ohi = 0u, onm = 0u, found = 0u;
     for (int b = 0; b < 32; ++b) {
         const uint32_t c = (vals[b >> 2] >> (8 * (b & 3))) & 0xffu;
         const uint32_t l = c | 0x20u;
         int code;
-        if (b >= vb) code = 4;
+        if (b < vlo || b >= vhi) code = 4;
         else if (l == 0x61u) code = 0;
         else if (l == 0x63u) code = 1;
         else if (l == 0x67u) code = 2;
         else if (l == 0x74u) code = 3;
         else {
             code = 4;
-            found |= (l != 0x6eu);
+            found |= (l != 0x6eu) ? 1u : 0u;
         }
         if (code == 4) onm |= 1u << b;
         else {
@@ -74,10 +104,7 @@ __device__ __forceinline__ bool slow_word(const uint32_t *vals, int vb, uint32_t
             if (code & 2) ohi |= 1u << b;
         }
     }
-    *lo = olo;
-    *hi = ohi;
-    *nm = onm;
-    return found;
+    return make_uint4(olo, ohi, onm, found);
 }
 
 // The 36 bytes that word w of a sequence needs, and where its bases start.
@@ -122,26 +149,20 @@ __device__ __forceinline__ void pack_decode(const PackWindow &pw, uint32_t *lo, 
     uint32_t v[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) v[i] = __funnelshift_r(pw.u[i], pw.u[i + 1], pw.sh);
-    uint32_t olo = 0u, ohi = 0u, onm = 0u, bad = 0u;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const uint32_t y = interleave_nibbles(v[2 * i], v[2 * i + 1]);
-        bad |= invalid8(v[2 * i], v[2 * i + 1], y);
-        const uint32_t t = y ^ (y >> 1);  // bit 1 of each nibble: bit1 ^ bit2
-        const uint32_t keep = 0xffu << (8 * i);
-        olo |= (gather8<1>(t) >> (24 - 8 * i)) & keep;
-        ohi |= (gather8<2>(y) >> (24 - 8 * i)) & keep;
-        onm |= (gather8<3>(y) >> (24 - 8 * i)) & keep;
-    }
-    if (bad) {
-        if (slow_word(v, pw.vb, lo, hi, nm)) atomicOr(err, ERR_BYTES);
+    uint32_t olo, ohi, onm;
+    if (decode32(v, olo, ohi, onm)) {
+        const uint4 r = slow_chunk(make_uint4(v[0], v[1], v[2], v[3]),
+                                   make_uint4(v[4], v[5], v[6], v[7]), 0, pw.vb);
+        if (r.w) atomicOr(err, ERR_BYTES);
+        *lo = r.x;
+        *hi = r.y;
+        *nm = r.z;
         return;
     }
     const uint32_t vmask = (pw.vb >= 32) ? 0xffffffffu : ((1u << pw.vb) - 1u);
-    onm |= ~vmask;      // bytes past the end are N
-    *lo = olo & ~onm;   // N carries code 00
-    *hi = ohi & ~onm;
-    *nm = onm;
+    *lo = olo & vmask;  // bytes past the end are N
+    *hi = ohi & vmask;
+    *nm = onm | ~vmask;
 }
 
 template <typename L = LdNC>

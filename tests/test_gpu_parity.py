@@ -178,6 +178,37 @@ def test_pack_neighbour_bytes_never_leak(pf, ctx):
             assert np.array_equal(got.cpu().numpy().view(np.uint32), want)
 
 
+@pytest.mark.parametrize("length,n", [(1, 5000), (2, 3001), (32, 2047), (150, 4000),
+                                      (4000, 300), (131072, 3), (131073, 2)])
+def test_pack_fixed_across_tiles(pf, ctx, length, n):
+    """The fixed layout over many 1023-word tiles with a ragged last one,
+    sources starting at every offset within 32 bytes after bytes that are
+    not bases, invalid bytes inside (packed as N, error raised), and the
+    longest sequences each kernel form takes (4096 words and one more)."""
+    from gpu_util import to_dev
+    rng = np.random.default_rng(length * 7 + n)
+    W = (length + 31) // 32
+    for shift in (0, 1, 7, 16, 31) if length < 100000 else (0, 13):
+        body = rng.choice(np.frombuffer(b"ACGTNacgtn", np.uint8), size=n * length)
+        bad_at = rng.choice(n * length, size=3, replace=False) if shift % 2 else []
+        body[bad_at] = np.frombuffer(b"X#-", np.uint8)[:len(bad_at)]
+        whole = np.concatenate([np.frombuffer(b"@" * shift, np.uint8), body,
+                                np.frombuffer(b"%" * 40, np.uint8)])
+        dev = to_dev(whole)
+        out = pf.Seqs.empty(n * W, "cuda:0", stride_words=W)
+        pf.pf_pack_fixed(ctx, dev[shift:shift + n * length], n, length, out)
+        if len(bad_at):
+            with pytest.raises(pf.PFError) as ei:
+                pf.pf_sync(ctx)
+            assert ei.value.status == 7
+        else:
+            pf.pf_sync(ctx)
+        _, lo, hi, nm, bad = oracle.pack_batch(body, np.arange(n + 1, dtype=np.int64) * length)
+        assert bad == len(bad_at)
+        for got, want in ((out.lo, lo), (out.hi, hi), (out.nmask, nm)):
+            assert np.array_equal(got.cpu().numpy().view(np.uint32), want), (shift, length)
+
+
 # ---- a2-a4 filter ---------------------------------------------------------
 
 CASES = [
