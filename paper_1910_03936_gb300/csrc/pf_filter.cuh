@@ -483,34 +483,34 @@ __device__ __forceinline__ int split_sneakysnake(const uint32_t *mine, int W, ui
     // word is the word's first step with every column open, and the
     // diagonals already blocked carry bit 0 set (blocked at once), which no
     // later step of the word looks at (they start past the first obstacle).
+    // Both ways into the next word share one block, so that a warp whose
+    // lanes cross words at different steps runs it once per step.
     for (;;) {
+        uint32_t y[NS];
         uint32_t T = 0xffffffffu;
 #pragma unroll
         for (int k = 0; k < NS; ++k) {
-            const uint32_t y = Mw[k] & C;
-            T &= y | (y * neg1);
+            y[k] = Mw[k] & C;
+            T &= y[k] | (y[k] * neg1);
         }
-        if (T == 0u) {  // the deepest pipe reaches the end of the word
-            if (ws == W - 1) break;
-            ++ws;
+        const int pbit = __ffs(T) - 1;  // the obstacle passed; -1 if T == 0
+        if (T != 0u) {
+            if (++kss > XE) break;
+            if (pbit != 31) {
+                C = 0xfffffffeu << pbit;
+                continue;
+            }
+        }
+        // Next word: after T == 0 the deepest pipe reaches the end of the
+        // word and the diagonals blocked in the rest of it stay blocked (bit
+        // 0 set, cm = 1); after an obstacle in the word's last column every
+        // diagonal starts free (cm = 0).
+        if (ws == W - 1) break;
+        ++ws;
+        const uint32_t cm = (T == 0u) ? 1u : 0u;
 #pragma unroll
-            for (int k = 0; k < NS; ++k)  // blocked in the rest of this word: blocked at once
-                Mw[k] = mine[(ws * NS + k) * 32] | ((Mw[k] & C) ? 1u : 0u);
-            C = 0xffffffffu;
-            continue;
-        }
-        const int pbit = __ffs(T) - 1;
-        ++kss;
-        if (kss > XE) break;
-        if (pbit == 31) {  // the obstacle was the word's last column
-            if (ws == W - 1) break;
-            ++ws;
-#pragma unroll
-            for (int k = 0; k < NS; ++k) Mw[k] = mine[(ws * NS + k) * 32];
-            C = 0xffffffffu;
-        } else {
-            C = 0xfffffffeu << pbit;
-        }
+        for (int k = 0; k < NS; ++k) Mw[k] = mine[(ws * NS + k) * 32] | min(y[k], cm);
+        C = 0xffffffffu;
     }
     return kss > XE + 1 ? XE + 1 : kss;
 }
