@@ -480,8 +480,29 @@ def main_gpu(args):
     n_idx = torch.empty(1, dtype=torch.int64, device=dev)
     pf.pf_compact(ctx, acc[:n], idx, n_idx, n)
     compact_ms = timed(lambda: pf.pf_compact(ctx, acc[:n], idx, n_idx, n))
+    verify_accepted_ms = timed(lambda: pf.pf_verify(ctx, pairs, lens, E, E_HEAD, idx, n_idx,
+                                                    dist_out, n))
+    n_accepted = int(n_idx.item())
+    # The step verifies only the accepted pairs whose SneakySnake count differs
+    # from their Hamming distance (the others are resolved by the filter).
+    # Rebuild that set here (Hamming distances by torch on the ASCII; N never
+    # matches) to time the verification the step runs; its size must equal
+    # the library's own count.
+    pf.pf_filter_verify(ctx, 3, pairs, lens, E, E_HEAD, acc, cnt, dist_out, n)
+    n_verified = pf.pf_last_verified_count(ctx)
+    need = torch.empty(n, dtype=torch.uint8, device=dev)
+    base = torch.tensor(list(b"ACGT"), dtype=torch.uint8, device=dev)
+    for c0 in range(0, n, 1 << 21):
+        c1 = min(n, c0 + (1 << 21))
+        r = reads[c0 * M:c1 * M].view(-1, M)
+        f = refs[c0 * M:c1 * M].view(-1, M)
+        ok = torch.isin(r, base) & torch.isin(f, base) & (r == f)
+        h = (M - ok.sum(1)).to(torch.int16)
+        need[c0:c1] = ((acc[c0:c1] == 1) & (cnt[c0:c1] != h)).to(torch.uint8)
+    pf.pf_compact(ctx, need, idx, n_idx, n)
+    assert int(n_idx.item()) == n_verified, (int(n_idx.item()), n_verified)
+    del need
     verify_ms = timed(lambda: pf.pf_verify(ctx, pairs, lens, E, E_HEAD, idx, n_idx, dist_out, n))
-    n_verified = int(n_idx.item())
     # the alternative to filtering: the early-exit verifier on every pair
     dist_all = torch.empty(n, dtype=torch.int32, device=dev)
     verify_all_ms = timed(lambda: pf.pf_verify(ctx, pairs, lens, E, E_HEAD, None, None,
@@ -592,12 +613,16 @@ def main_gpu(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "pairs_per_gpu": n, "read_len": M, "E": E_HEAD,
-                   "deciders": "SneakySnake+GateKeeper", "verify": "SneakySnake accepts",
+                   "deciders": "SneakySnake+GateKeeper",
+                   "verify": "SneakySnake accepts whose count differs from their Hamming "
+                             "distance (equal bounds resolve the rest)",
                    "l2": "inputs larger than L2 (9 GB resident)"},
         "stages_ms": {"pack": pack_ms, "filter_compact_verify": fv_ms, "filter": filt_ms,
                       "compact": compact_ms, "verify": verify_ms,
+                      "verify_every_accepted_pair": verify_accepted_ms,
                       "verify_all_pairs_instead": verify_all_ms},
-        "accepted_frac": n_verified / n,
+        "accepted_frac": n_accepted / n,
+        "verified_frac": n_verified / n,
         "filter_sneakysnake": {"batched_pairs_s": n / (ss_batched_ms / 1000.0),
                                "plain_pairs_s": n / (ss_plain_ms / 1000.0),
                                "batched_over_plain": ss_plain_ms / ss_batched_ms,

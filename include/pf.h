@@ -211,6 +211,13 @@ PF_API pf_status pf_tune_batch(pf_ctx *ctx, unsigned deciders, const pf_pairs *p
  * batched scheduler.  PF_EINVAL for pairs < 0. */
 PF_API pf_status pf_set_small_batch(pf_ctx *ctx, int64_t pairs);
 
+/* enable != 0 (the default): pf_filter_verify and pf_run_host with both
+ * deciders leave out of verification the accepted pairs whose SneakySnake
+ * count equals their Hamming distance, whose distance is then known (see
+ * pf_filter_verify); 0 verifies every accepted pair.  Results are the same
+ * either way.  PF_EINVAL only for a NULL context. */
+PF_API pf_status pf_set_resolve_by_bounds(pf_ctx *ctx, int enable);
+
 /* Use configuration cfg and a work chunk of `chunk` pairs (1..65536) for
  * threshold E under decider set `deciders` in later pf_filter calls.
  * PF_EINVAL if cfg cannot serve E. */
@@ -310,10 +317,20 @@ PF_API pf_status pf_verify(pf_ctx *ctx, const pf_pairs *pairs, const int32_t *le
 
 /* Whole path for n pairs: filter (deciders as in pf_filter), compact the
  * pairs the first selected decider accepts, verify them; dist[p] =
- * min(ED, E+1) for those and E + 1 for every rejected pair. */
+ * min(ED, E+1) for those and E + 1 for every rejected pair.  With both
+ * deciders, an accepted pair whose SneakySnake count equals its Hamming
+ * distance (a lower and an upper bound on its banded edit distance) gets
+ * that count as dist from the filter and is not verified (the same value
+ * the verifier would write); pf_set_resolve_by_bounds turns this off. */
 PF_API pf_status pf_filter_verify(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs,
                            const int32_t *lens, const int16_t *E, int E_max,
                            uint8_t *accept, int16_t *count, int32_t *dist, int64_t n);
+
+/* The number of pairs the most recent pf_filter_verify on this context sent
+ * to verification (its accepted pairs less those resolved by equal bounds).
+ * Synchronises the context stream.  PF_EINVAL if there is no such call, or
+ * if a later call on the context reallocated its scratch memory. */
+PF_API pf_status pf_last_verified_count(pf_ctx *ctx, int64_t *n_verified);
 
 /* ---- a7: the whole path on host buffers, chunked and graph-replayed ------ */
 

@@ -23,7 +23,8 @@ __all__ = [
     "ServeConfig", "Request", "pf_serve_start", "pf_submit", "pf_poll", "pf_wait",
     "pf_serve_resume", "pf_serve_stats_get", "pf_serve_stop", "pf_serve_replay", "pf_run_host",
     "pf_filter_partitioned", "pf_filter_shouji", "pf_filter_shd", "PF_SHD_VACANT_ZERO",
-    "PF_SHD_STREAK", "pf_set_small_batch", "pf_tune_batch",
+    "PF_SHD_STREAK", "pf_set_small_batch", "pf_tune_batch", "pf_set_resolve_by_bounds",
+    "pf_last_verified_count",
 ]
 
 PF_SNEAKYSNAKE = 1
@@ -127,6 +128,8 @@ def load():
         "pf_serve_replay": [P, P, I, P, I, P, ctypes.POINTER(ctypes.c_double)],
         "pf_tune_set": [P, U, I, I, I],
         "pf_set_small_batch": [P, I64],
+        "pf_set_resolve_by_bounds": [P, I],
+        "pf_last_verified_count": [P, ctypes.POINTER(ctypes.c_int64)],
         "pf_tune_batch": [P, U, ctypes.POINTER(_Pairs), P, P, I, I64, I64, I],
         "pf_tune_get": [P, U, I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
         "pf_tune": [P, U, ctypes.POINTER(_Pairs), P, I, I64, I, ctypes.POINTER(ctypes.c_int),
@@ -438,6 +441,19 @@ def pf_tune_batch(ctx, deciders, pairs, lens, E, E_max, n=None, sample=0, reps=2
 def pf_set_small_batch(ctx, pairs):
     """Batches below `pairs` take one plain launch (0: always the scheduler)."""
     _check(load().pf_set_small_batch(ctx.handle, int(pairs)), ctx.handle)
+
+
+def pf_set_resolve_by_bounds(ctx, enable):
+    """Skip verifying accepted pairs whose SneakySnake count equals their
+    Hamming distance (default on; results are the same either way)."""
+    _check(load().pf_set_resolve_by_bounds(ctx.handle, int(bool(enable))), ctx.handle)
+
+
+def pf_last_verified_count(ctx):
+    """Pairs the last pf_filter_verify on ctx sent to verification."""
+    v = ctypes.c_int64()
+    _check(load().pf_last_verified_count(ctx.handle, ctypes.byref(v)), ctx.handle)
+    return v.value
 
 
 def pf_tune_get(ctx, deciders, E):

@@ -127,6 +127,7 @@ pf_status pf_ctx::cuda(cudaError_t e, const char *what) {
 
 pf_status pf_ctx::ensure_scratch(size_t bytes) {
     if (bytes <= scratch_bytes) return PF_OK;
+    verified_valid = false;
     if (scratch) {
         cudaStreamSynchronize(stream);
         cudaFree(scratch);
@@ -152,15 +153,16 @@ pf_status pf_ctx::scratch_layout(int64_t n, Scratch *s) {
     auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
     const size_t nn = (size_t)std::max<int64_t>(n, 1);
     size_t off = 0;
+    const size_t o_nidx = off;  off += up(sizeof(int64_t));  // first: pf_last_verified_count
     const size_t o_order = off; off += up(nn * sizeof(int64_t));
     const size_t o_idx = off;   off += up(nn * sizeof(int64_t));
-    const size_t o_nidx = off;  off += up(sizeof(int64_t));
     const size_t o_tiles = off; off += up((size_t)compact_tiles((int64_t)nn) * sizeof(int64_t));
     const size_t o_bins = off;  off += up((kNumBatchCfgs + 1) * sizeof(int64_t));
     const size_t o_work = off;  off += up(kNumBatchCfgs * sizeof(unsigned long long));
     const size_t o_hist = off;  off += up(kNumBatchCfgs * sizeof(unsigned long long));
     const size_t o_cur = off;   off += up(kNumBatchCfgs * sizeof(unsigned long long));
     const size_t o_ident = off; off += up(sizeof(int));
+    const size_t o_need = off;  off += up(nn);
     pf_status st = ensure_scratch(off);
     if (st != PF_OK) return st;
     char *b = static_cast<char *>(scratch);
@@ -173,6 +175,7 @@ pf_status pf_ctx::scratch_layout(int64_t n, Scratch *s) {
     s->hist = reinterpret_cast<unsigned long long *>(b + o_hist);
     s->cursor = reinterpret_cast<unsigned long long *>(b + o_cur);
     s->ident = reinterpret_cast<int *>(b + o_ident);
+    s->need = reinterpret_cast<uint8_t *>(b + o_need);
     return PF_OK;
 }
 
@@ -404,6 +407,12 @@ pf_status pf_set_stream(pf_ctx *ctx, void *stream) {
     return PF_OK;
 }
 
+pf_status pf_set_resolve_by_bounds(pf_ctx *ctx, int enable) {
+    if (!ctx) return PF_EINVAL;
+    ctx->resolve_bounds = enable != 0;
+    return PF_OK;
+}
+
 pf_status pf_sync(pf_ctx *ctx) {
     if (!ctx) return PF_EINVAL;
     cudaSetDevice(ctx->device);
@@ -555,15 +564,35 @@ pf_status pf_filter_verify(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs
     if (st != PF_OK) return st;
     FilterArgs a = make_filter_args(ctx, pairs, lens, E, E_max, accept, count, n);
     a.dist = dist;  // the filter writes E + 1 for the pairs it rejects
+    // with both deciders the filter also resolves the pairs whose obstacle
+    // count equals their Hamming distance
+    if (ctx->resolve_bounds && (deciders & 3u) == 3u) a.need = s.need;
     st = ctx->run_filter(deciders, a, s);
     if (st != PF_OK) return st;
-    // the first selected decider's accept flags choose the pairs to verify
-    st = ctx->cuda(launch_compact(accept, n, s.idx, s.n_idx, s.tiles, ctx->stream),
+    // the first selected decider's accept flags (less the resolved pairs)
+    // choose the pairs to verify
+    st = ctx->cuda(launch_compact(a.need ? a.need : accept, n, s.idx, s.n_idx, s.tiles,
+                                  ctx->stream),
                    "compact launch");
     if (st != PF_OK) return st;
-    return ctx->cuda(launch_verify(to_view(pairs), lens, E, E_max, s.idx, s.n_idx, n, dist,
-                                   ctx->d_err, ctx->sms, ctx->stream),
-                     "verify launch");
+    st = ctx->cuda(launch_verify(to_view(pairs), lens, E, E_max, s.idx, s.n_idx, n, dist,
+                                 ctx->d_err, ctx->sms, ctx->stream),
+                   "verify launch");
+    ctx->verified_valid = st == PF_OK;
+    return st;
+}
+
+pf_status pf_last_verified_count(pf_ctx *ctx, int64_t *n_verified) {
+    if (!ctx) return PF_EINVAL;
+    if (!n_verified) return ctx->fail(PF_EINVAL, "null pointer argument");
+    if (!ctx->verified_valid || !ctx->scratch)
+        return ctx->fail(PF_EINVAL, "no pf_filter_verify result on this context");
+    cudaSetDevice(ctx->device);
+    pf_status st = ctx->cuda(cudaMemcpyAsync(n_verified, ctx->scratch, sizeof(int64_t),
+                                             cudaMemcpyDeviceToHost, ctx->stream),
+                             "count copy");
+    if (st == PF_OK) st = ctx->cuda(cudaStreamSynchronize(ctx->stream), "stream sync");
+    return st;
 }
 
 pf_status pf_kernel_configs(int *tpp, int *dpt, int *ecap, int *exact_e, int *words, int cap,

@@ -17,6 +17,7 @@ struct Scratch {
     int64_t *order, *idx, *n_idx, *tiles, *bin_start;
     unsigned long long *work, *hist, *cursor;
     int *ident;
+    uint8_t *need;   // pairs left to verify (see FilterArgs::need)
 };
 
 struct ServeState;
@@ -49,6 +50,8 @@ struct pf_ctx {
     // batches of fewer pairs take one plain launch (no binning, no per-bin
     // launches); 0 sends every batch through the batched scheduler
     int64_t small_batch = int64_t(1) << 20;
+    bool resolve_bounds = true;  // skip verifying pairs whose count bounds agree
+    bool verified_valid = false; // scratch holds the last pf_filter_verify's count
     int grid_cache[4][pf::kNumBatchCfgs] = {};
 
     cudaStream_t side_streams[pf::kSideStreams] = {};

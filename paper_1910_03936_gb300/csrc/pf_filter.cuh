@@ -366,10 +366,24 @@ struct PairFilter {
     }
 };
 
+// h: GateKeeper's Hamming count (the d = 0 diagonal's mismatches), exact
+// whenever it is <= E.  SneakySnake's obstacle count never exceeds the edit
+// distance within the band (each edit of a banded alignment costs the snake
+// at most one obstacle, and the greedy walk needs the fewest, Ch. 8), and the
+// Hamming distance never falls below it (substitutions alone align the
+// pair on d = 0).  When the two agree the distance is known: with a.need set
+// such a pair is written here and left out of verification.
 template <int DEC>
 __device__ __forceinline__ void write_outputs(const FilterArgs &a, int64_t p, int E, int ssc,
-                                              int gkc) {
+                                              int gkc, int h) {
     if (a.dist && (DEC == 2 ? gkc : ssc) > E) a.dist[p] = E + 1;  // not verified
+    if constexpr (DEC == 3) {
+        if (a.need) {
+            const bool known = ssc <= E && h == ssc;
+            a.need[p] = (uint8_t)(ssc <= E && !known);
+            if (known) a.dist[p] = h;
+        }
+    }
     if constexpr (DEC == 3) {
         a.count[p] = (int16_t)ssc;
         a.accept[p] = (uint8_t)(ssc <= E);
@@ -392,6 +406,7 @@ __device__ __forceinline__ void write_invalid(const FilterArgs &a, int64_t p) {
     if constexpr (DEC == 3) {
         a.count[a.n + p] = -1;
         a.accept[a.n + p] = 0;
+        if (a.need) a.need[p] = 0;
     }
     atomicOr(a.err, ERR_PAIR_ARGS);
 }
@@ -420,7 +435,7 @@ __device__ __forceinline__ void filter_group(const FilterArgs &a, int64_t p, int
     st.run(a.pairs, g, gmask);
     int ssc = 0, gkc = 0;
     st.finish(g, gmask, &ssc, &gkc);
-    if (g == 0) write_outputs<DEC>(a, p, E, ssc, gkc);
+    if (g == 0) write_outputs<DEC>(a, p, E, ssc, gkc, st.h);
 }
 
 // The plain kernel: one thread per pair, every thread runs its own pair to
@@ -532,7 +547,7 @@ __device__ __forceinline__ void filter_split_pair(const FilterArgs &a, int64_t p
     int ssc = 0, gkc = 0;
     st.finish(0, lane_mask, &ssc, &gkc);
     if constexpr (DEC & 1) ssc = split_sneakysnake<XE>(mine, W, st.neg1);
-    write_outputs<DEC>(a, p, E, ssc, gkc);
+    write_outputs<DEC>(a, p, E, ssc, gkc, st.h);
 }
 
 // Shared memory: kSplitWarps warps x WMAX words x (2 XE + 1) slots x 32 lanes.

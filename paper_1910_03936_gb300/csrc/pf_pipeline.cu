@@ -92,7 +92,7 @@ pf_status alloc_slot(Job &J, Slot &s) {
                  o_tiles = add((size_t)compact_tiles((int64_t)C) * 8),
                  o_bins = add((kNumBatchCfgs + 1) * 8), o_work = add(kNumBatchCfgs * 8),
                  o_hist = add(kNumBatchCfgs * 8), o_cur = add(kNumBatchCfgs * 8),
-                 o_ident = add(4);
+                 o_ident = add(4), o_need = add(C);
     if (cudaMalloc(&s.mem, o) != cudaSuccess) {
         cudaGetLastError();
         return J.ctx->fail(PF_ENOMEM, "pf_run_host: %zu device bytes per slot", o);
@@ -118,6 +118,7 @@ pf_status alloc_slot(Job &J, Slot &s) {
     s.scr.hist = reinterpret_cast<unsigned long long *>(m + o_hist);
     s.scr.cursor = reinterpret_cast<unsigned long long *>(m + o_cur);
     s.scr.ident = reinterpret_cast<int *>(m + o_ident);
+    s.scr.need = reinterpret_cast<uint8_t *>(m + o_need);
     if (cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&s.ev_done, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
@@ -171,12 +172,13 @@ pf_status enqueue_chunk(Job &J, Slot &s, int64_t nc) {
     a.n = nc;
     a.err = ctx->d_err;
     a.dist = s.dist;  // E + 1 for the pairs the filter rejects
+    if (ctx->resolve_bounds && (J.dec & 3u) == 3u) a.need = s.scr.need;
     cudaStream_t saved = ctx->stream;
     ctx->stream = s.st;
     pf_status st = ctx->run_filter(J.dec, a, s.scr);
     ctx->stream = saved;
     if (st != PF_OK) return st;
-    e = launch_compact(s.acc, nc, s.scr.idx, s.scr.n_idx, s.scr.tiles, s.st);
+    e = launch_compact(a.need ? a.need : s.acc, nc, s.scr.idx, s.scr.n_idx, s.scr.tiles, s.st);
     if (e == cudaSuccess)
         e = launch_verify(pv, s.lens, a.E, J.E_max, s.scr.idx, s.scr.n_idx, nc, s.dist,
                           ctx->d_err, ctx->sms, s.st);

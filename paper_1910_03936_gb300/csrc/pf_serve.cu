@@ -144,7 +144,7 @@ __device__ __forceinline__ void serve_filter_chunk(const ServeDesc &d, const Pai
         st.run(pv, g, gmask);
         int ssc = 0, gkc = 0;
         st.finish(g, gmask, &ssc, &gkc);
-        if (g == 0) write_outputs<DEC>(a, p, E, ssc, gkc);
+        if (g == 0) write_outputs<DEC>(a, p, E, ssc, gkc, st.h);
     }
 }
 

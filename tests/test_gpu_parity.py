@@ -437,6 +437,42 @@ def test_filter_verify_path(pf, ctx, case_data, name):
     assert np.all(oa[0][vb <= P.E] == 1)
 
 
+@pytest.mark.parametrize("name", [c[0] for c in CASES])
+@pytest.mark.parametrize("small", [0, 1 << 30])
+def test_resolved_pairs_equal_full_verification(pf, ctx, case_data, name, small):
+    """Accepted pairs whose SneakySnake count equals their Hamming distance
+    skip verification; their distances (and every other output) equal those
+    of verifying every accepted pair, and the oracle's, through the
+    scheduler's kernels and through the plain kernel."""
+    P, D, (oa, oc) = case_data[name]
+    n = D.n
+    vb = oracle.verify_batch(P)
+    want = np.where(oa[0] == 1, vb, P.E.astype(np.int32) + 1)
+    outs, counts = [], []
+    pf.pf_set_small_batch(ctx, small)
+    try:
+        for resolve in (True, False):
+            pf.pf_set_resolve_by_bounds(ctx, resolve)
+            acc = torch.zeros(2 * n, dtype=torch.uint8, device="cuda:0")
+            cnt = torch.zeros(2 * n, dtype=torch.int16, device="cuda:0")
+            dist = torch.full((n,), -5, dtype=torch.int32, device="cuda:0")
+            pf.pf_filter_verify(ctx, 3, D.pairs, D.lens, D.E, D.E_max, acc, cnt, dist, n)
+            pf.pf_sync(ctx)
+            outs.append((acc.cpu().numpy(), cnt.cpu().numpy(), dist.cpu().numpy()))
+            counts.append(pf.pf_last_verified_count(ctx))
+    finally:
+        pf.pf_set_resolve_by_bounds(ctx, True)
+        pf.pf_set_small_batch(ctx, 0)
+    for x, y in zip(outs[0], outs[1]):
+        assert np.array_equal(x, y)
+    assert np.array_equal(outs[0][2], want)
+    assert np.array_equal(outs[0][0].reshape(2, n), oa)
+    ham = oracle.int_batch("hamming", P)
+    resolved = (oa[0] == 1) & (oc[0] == ham)
+    assert np.array_equal(outs[0][2][resolved], ham[resolved])
+    assert counts == [int(oa[0].sum() - resolved.sum()), int(oa[0].sum())]
+
+
 def test_two_phase_configs_on_ragged_pairs(pf, ctx, case_data):
     """The two-phase kernels on mixed lengths and thresholds: pairs longer
     than their shared arrays take the fused loop in the same warps."""

@@ -325,6 +325,34 @@ def test_substitution_only_bounded_by_hamming():
         assert np.array_equal(cnt[1][sel], ham[sel])
 
 
+@pytest.mark.parametrize("E", [0, 1, 2, 3, 5])
+def test_equal_bounds_give_the_distance(exhaustive_5, E):
+    """SneakySnake's count is a lower bound on the banded distance (Ch. 8
+    Discussion: the snake underestimates the edits) and the Hamming distance
+    an upper one (substitutions alone align the pair), so where the two agree
+    at <= E that is the distance: the pairs the path resolves without
+    verification."""
+    reads, refs = exhaustive_5
+    P = ArrayPairs(reads, refs, E)
+    _, cnt = oracle.filter_batch(P)
+    ham = oracle.int_batch("hamming", P)
+    wfb = oracle.int_batch("wf_banded", P)
+    ss = cnt[0].astype(np.int32)
+    assert np.all(ss <= wfb) and np.all(wfb <= np.minimum(ham, E + 1))
+    sel = (ss == ham) & (ham <= E)
+    assert sel.any() and np.array_equal(wfb[sel], ham[sel])
+
+
+def test_equal_bounds_give_the_distance_synthetic():
+    P = synth.generate(synth.SKEWED, 0x5EED0B0D, 3000, m=150, E=6, kmax=20)
+    _, cnt = oracle.filter_batch(P)
+    ham = oracle.int_batch("hamming", P)
+    wfb = oracle.verify_batch(P)
+    sel = (cnt[0] == ham) & (ham <= 6)
+    assert sel.sum() > 100
+    assert np.array_equal(wfb[sel], ham[sel])
+
+
 @pytest.mark.parametrize("m,E,kind", [(100, 5, synth.UNIFORM), (150, 6, synth.SKEWED),
                                       (250, 25, synth.SKEWED_ALL)])
 def test_zero_false_rejects_on_synthetic_reads(m, E, kind):
