@@ -580,10 +580,11 @@ def main_gpu(args):
     # DRAM bytes per launch from one ncu capture of each kernel at 2M pairs
     # (profiles/), scaled to this launch by the units processed; valid for
     # the kernels as captured (the two-phase exact-E6 filter with 5-word
-    # arrays that the tuner picks, pack_fixed, verify<u32>)
-    traffic_per_pair = {"filter": (248.206336e6 + 11.1616e6) / 2e6,
-                        "pack": 2 * (300.065024e6 + 94.899712e6) / 4e6,
-                        "verify": (223.07456e6 + 6.509312e6) / 2e6}
+    # arrays that the tuner picks; pack_stream, one launch per 2M sequences,
+    # two per pair; verify<u32> on the pairs left after equal bounds)
+    traffic_per_pair = {"filter": (248.146432e6 + 11.001856e6) / 2e6,
+                        "pack": 2 * (300.083456e6 + 92.212992e6) / 2e6,
+                        "verify": (173.886208e6 + 5.08544e6) / 2e6}
     sm_mhz = clk.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
     alu_peak = 152 * 64 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # Top/s, ALU pipe
     ms_dom = stages[dominant]
