@@ -211,8 +211,8 @@ PF_API pf_status pf_tune_batch(pf_ctx *ctx, unsigned deciders, const pf_pairs *p
  * batched scheduler.  PF_EINVAL for pairs < 0. */
 PF_API pf_status pf_set_small_batch(pf_ctx *ctx, int64_t pairs);
 
-/* enable != 0 (the default): pf_filter_verify and pf_run_host with both
- * deciders leave out of verification the accepted pairs whose SneakySnake
+/* enable != 0 (the default): pf_filter_verify and pf_run_host with
+ * SneakySnake selected leave out of verification the accepted pairs whose SneakySnake
  * count equals their Hamming distance, whose distance is then known (see
  * pf_filter_verify); 0 verifies every accepted pair.  Results are the same
  * either way.  PF_EINVAL only for a NULL context. */
@@ -317,8 +317,8 @@ PF_API pf_status pf_verify(pf_ctx *ctx, const pf_pairs *pairs, const int32_t *le
 
 /* Whole path for n pairs: filter (deciders as in pf_filter), compact the
  * pairs the first selected decider accepts, verify them; dist[p] =
- * min(ED, E+1) for those and E + 1 for every rejected pair.  With both
- * deciders, an accepted pair whose SneakySnake count equals its Hamming
+ * min(ED, E+1) for those and E + 1 for every rejected pair.  With
+ * SneakySnake selected, an accepted pair whose obstacle count equals its Hamming
  * distance (a lower and an upper bound on its banded edit distance) gets
  * that count as dist from the filter and is not verified (the same value
  * the verifier would write); pf_set_resolve_by_bounds turns this off. */

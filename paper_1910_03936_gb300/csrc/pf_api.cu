@@ -564,9 +564,9 @@ pf_status pf_filter_verify(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs
     if (st != PF_OK) return st;
     FilterArgs a = make_filter_args(ctx, pairs, lens, E, E_max, accept, count, n);
     a.dist = dist;  // the filter writes E + 1 for the pairs it rejects
-    // with both deciders the filter also resolves the pairs whose obstacle
-    // count equals their Hamming distance
-    if (ctx->resolve_bounds && (deciders & 3u) == 3u) a.need = s.need;
+    // with SneakySnake selected the filter also resolves the pairs whose
+    // obstacle count equals their Hamming distance
+    if (ctx->resolve_bounds && (deciders & 1u)) a.need = s.need;
     st = ctx->run_filter(deciders, a, s);
     if (st != PF_OK) return st;
     // the first selected decider's accept flags (less the resolved pairs)

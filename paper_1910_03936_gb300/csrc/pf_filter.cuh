@@ -296,6 +296,12 @@ struct PairFilter {
             }
         }
 
+        // ---- Hamming count alone (SneakySnake without GateKeeper): lane 0
+        // owns d = 0 and writes the outputs
+        if constexpr (!GK && (SS || SINK)) {
+            if (g == 0) h += __popc(M[0]);
+        }
+
         // ---- GateKeeper: Hamming word, amend + AND of the previous word
         if constexpr (GK) {
             if (!gk_done) {
@@ -366,8 +372,8 @@ struct PairFilter {
     }
 };
 
-// h: GateKeeper's Hamming count (the d = 0 diagonal's mismatches), exact
-// whenever it is <= E.  SneakySnake's obstacle count never exceeds the edit
+// h: the Hamming count (the d = 0 diagonal's mismatches), exact whenever
+// it is <= E and SneakySnake accepts (every word is then processed).  SneakySnake's obstacle count never exceeds the edit
 // distance within the band (each edit of a banded alignment costs the snake
 // at most one obstacle, and the greedy walk needs the fewest, Ch. 8), and the
 // Hamming distance never falls below it (substitutions alone align the
@@ -377,7 +383,7 @@ template <int DEC>
 __device__ __forceinline__ void write_outputs(const FilterArgs &a, int64_t p, int E, int ssc,
                                               int gkc, int h) {
     if (a.dist && (DEC == 2 ? gkc : ssc) > E) a.dist[p] = E + 1;  // not verified
-    if constexpr (DEC == 3) {
+    if constexpr (DEC & 1) {
         if (a.need) {
             const bool known = ssc <= E && h == ssc;
             a.need[p] = (uint8_t)(ssc <= E && !known);
@@ -406,6 +412,8 @@ __device__ __forceinline__ void write_invalid(const FilterArgs &a, int64_t p) {
     if constexpr (DEC == 3) {
         a.count[a.n + p] = -1;
         a.accept[a.n + p] = 0;
+    }
+    if constexpr (DEC & 1) {
         if (a.need) a.need[p] = 0;
     }
     atomicOr(a.err, ERR_PAIR_ARGS);

@@ -86,7 +86,7 @@ struct FilterArgs {
     int64_t n = 0;
     unsigned *err = nullptr;
     int32_t *dist = nullptr;  // non-null: E + 1 for pairs the first decider rejects, -1 if invalid
-    // Non-null (both deciders only): 1 for the SneakySnake-accepted pairs that
+    // Non-null (SneakySnake selected only): 1 for the SneakySnake-accepted pairs that
     // still need verification; a pair whose obstacle count equals its Hamming
     // distance gets 0 here and that count as its distance in dist.
     uint8_t *need = nullptr;

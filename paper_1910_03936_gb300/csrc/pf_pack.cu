@@ -9,13 +9,77 @@ namespace pf {
 
 namespace {
 
-constexpr int kSeqPerBlock = 128;
 constexpr int kPackThreads = 256;
+
+// Chunks.  Chunk j of a buffer is its 32 bytes from A + 32 j, A = an
+// address rounded down to 32 bytes; decoded, it is one word per plane whose
+// bit b is byte A + 32 j + b, so the word of a sequence that starts at byte
+// P of that stream is the stream's 32 bits from P: one funnel shift per
+// plane over two chunk words.  A block decodes up to 4 chunks per thread,
+// two 16-byte loads each (coalesced across the warp, no re-reads).
+constexpr int kStreamChunksPerThread = 4;
+constexpr int kStreamChunks = kStreamChunksPerThread * kPackThreads;  // fixed layout
+constexpr int kStreamWords = kStreamChunks - 1;
+
+// Decode chunks [0, nchunks) from cbase (32-byte aligned) into chunk[].
+// Bytes of [vbeg, vend) are the sequences'; the 4-byte words that hold
+// them are read, others count as "NNNN"; a byte outside [vbeg, vend) that
+// is not a base never raises the error.
+template <int THREADS>
+__device__ __forceinline__ void decode_chunks(uintptr_t cbase, int nchunks, uintptr_t vbeg,
+                                              uintptr_t vend, uint4 *chunk, unsigned *err) {
+    const uintptr_t lo4 = vbeg & ~uintptr_t(3), hi4 = (vend + 3) & ~uintptr_t(3);
+    uint32_t v[kStreamChunksPerThread][8];
+#pragma unroll
+    for (int r = 0; r < kStreamChunksPerThread; ++r) {
+        const int c = threadIdx.x + r * THREADS;
+        if (c >= nchunks) continue;
+        const uintptr_t ca = cbase + 32 * (uintptr_t)c;
+        if (ca >= lo4 && ca + 32 <= hi4) {
+            const uint4 x0 = __ldg(reinterpret_cast<const uint4 *>(ca));
+            const uint4 x1 = __ldg(reinterpret_cast<const uint4 *>(ca + 16));
+            v[r][0] = x0.x; v[r][1] = x0.y; v[r][2] = x0.z; v[r][3] = x0.w;
+            v[r][4] = x1.x; v[r][5] = x1.y; v[r][6] = x1.z; v[r][7] = x1.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const uintptr_t wa = ca + 4 * k;
+                v[r][k] = (wa >= lo4 && wa < hi4) ? __ldg(reinterpret_cast<const uint32_t *>(wa))
+                                                  : 0x4e4e4e4eu;
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < kStreamChunksPerThread; ++r) {
+        const int c = threadIdx.x + r * THREADS;
+        if (c >= nchunks) continue;
+        uint32_t l, h, n;
+        if (decode32(v[r], l, h, n)) {
+            const uintptr_t ca = cbase + 32 * (uintptr_t)c;
+            const int vlo = (vbeg > ca) ? (int)(vbeg - ca) : 0;
+            const int vhi = (vend < ca + 32) ? (int)((intptr_t)vend - (intptr_t)ca) : 32;
+            const uint4 e = slow_chunk(make_uint4(v[r][0], v[r][1], v[r][2], v[r][3]),
+                                       make_uint4(v[r][4], v[r][5], v[r][6], v[r][7]), vlo, vhi);
+            if (e.w) atomicOr(err, ERR_BYTES);
+            l = e.x;
+            h = e.y;
+            n = e.z;
+        }
+        chunk[c] = make_uint4(l, h, n, 0u);
+    }
+}
 
 // Ragged layout: block handles sequences [s0, s0 + kSeqPerBlock); its
 // threads walk the block's words, finding each word's sequence by a binary
-// search over the staged word offsets.
-__global__ void __launch_bounds__(kPackThreads)
+// search over the staged word offsets, and decode each word from its own
+// 32-byte window.  (Decoding the block's bytes as one chunk stream first, as
+// the fixed layout does, was slower here: the extra round of memory latency
+// for the offsets and the binary search per word left too little work per
+// block to hide it.)  Words past ceil(len/32) of a sequence (a word_off
+// with room to spare) are all N.
+constexpr int kSeqPerBlock = 128;
+
+__global__ void __launch_bounds__(kPackThreads, 8)
 pack_ragged_kernel(const uint8_t *ascii, const int64_t *byte_off, const int64_t *word_off,
                    int64_t nseq, uint32_t *lo, uint32_t *hi, uint32_t *nm, unsigned *err) {
     __shared__ int64_t woff[kSeqPerBlock + 1];
@@ -39,6 +103,12 @@ pack_ragged_kernel(const uint8_t *ascii, const int64_t *byte_off, const int64_t 
         }
         const int w = (int)(gw - woff[l]);
         const int len = (int)(boff[l + 1] - boff[l]);
+        if (len - 32 * w <= 0) {
+            lo[gw] = 0u;
+            hi[gw] = 0u;
+            nm[gw] = 0xffffffffu;
+            continue;
+        }
         pack_word(ascii + boff[l], len, w, lo + gw, hi + gw, nm + gw, err, lim);
     }
 }
@@ -85,19 +155,12 @@ pack_fixed_kernel(const uint8_t *ascii, int64_t nseq, int len, int W, uint32_t w
     }
 }
 
-// Stream-tiled fixed layout.  Chunk j of the buffer is its 32 bytes from
-// A + 32 j, A = the buffer start rounded down to 32 bytes; decoded, it is
-// one word per plane whose bit b is byte A + 32 j + b.  Word w of sequence
-// s is the 32 bits of that stream from byte s*len + 32 w, one funnel shift
-// per plane over two chunk words.  A block packs kStreamWords consecutive
-// words (s-major): their start bytes rise by at most 32 from one word to
-// the next, so they span at most kStreamWords + 1 chunks, which the block
-// decodes into shared memory first (two 16-byte loads per chunk, no
-// re-reads), then cuts out its words.
-constexpr int kStreamWords = 1023;
-constexpr int kStreamChunksPerThread = (kStreamWords + 1) / kPackThreads;
-static_assert(kStreamChunksPerThread * kPackThreads == kStreamWords + 1, "chunk split");
-
+// Stream-tiled fixed layout: word w of sequence s starts at byte s*len + 32 w
+// of the buffer.  A block packs kStreamWords consecutive words (s-major):
+// their start bytes rise by at most 32 from one word to the next, so they
+// span at most kStreamWords + 1 chunks (from A = the buffer start rounded
+// down to 32 bytes), which the block decodes into shared memory first, then
+// cuts out its words.
 __global__ void __launch_bounds__(kPackThreads, 4)
 pack_stream_kernel(const uint8_t *ascii, int64_t nseq, int len, int W, uint32_t wmagic,
                    uint32_t *lo, uint32_t *hi, uint32_t *nm, unsigned *err) {
@@ -124,48 +187,9 @@ pack_stream_kernel(const uint8_t *ascii, int64_t nseq, int len, int W, uint32_t 
     __syncthreads();
     const int nchunks = s_nchunks;
     const uintptr_t cbase = A + 32 * (uintptr_t)s_j0;
-    // bytes of the buffer, and the 4-byte words that hold them
+    // the bytes of the buffer
     const uintptr_t vbeg = src, vend = src + (uintptr_t)(nseq * (int64_t)len);
-    const uintptr_t lo4 = vbeg & ~uintptr_t(3), hi4 = (vend + 3) & ~uintptr_t(3);
-
-    uint32_t v[kStreamChunksPerThread][8];
-#pragma unroll
-    for (int r = 0; r < kStreamChunksPerThread; ++r) {
-        const int c = threadIdx.x + r * kPackThreads;
-        if (c >= nchunks) continue;
-        const uintptr_t ca = cbase + 32 * (uintptr_t)c;
-        if (ca >= lo4 && ca + 32 <= hi4) {
-            const uint4 x0 = __ldg(reinterpret_cast<const uint4 *>(ca));
-            const uint4 x1 = __ldg(reinterpret_cast<const uint4 *>(ca + 16));
-            v[r][0] = x0.x; v[r][1] = x0.y; v[r][2] = x0.z; v[r][3] = x0.w;
-            v[r][4] = x1.x; v[r][5] = x1.y; v[r][6] = x1.z; v[r][7] = x1.w;
-        } else {
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const uintptr_t wa = ca + 4 * k;
-                v[r][k] = (wa >= lo4 && wa < hi4) ? __ldg(reinterpret_cast<const uint32_t *>(wa))
-                                                  : 0x4e4e4e4eu;
-            }
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < kStreamChunksPerThread; ++r) {
-        const int c = threadIdx.x + r * kPackThreads;
-        if (c >= nchunks) continue;
-        uint32_t l, h, n;
-        if (decode32(v[r], l, h, n)) {
-            const uintptr_t ca = cbase + 32 * (uintptr_t)c;
-            const int vlo = (vbeg > ca) ? (int)(vbeg - ca) : 0;
-            const int vhi = (vend < ca + 32) ? (int)((intptr_t)vend - (intptr_t)ca) : 32;
-            const uint4 e = slow_chunk(make_uint4(v[r][0], v[r][1], v[r][2], v[r][3]),
-                                       make_uint4(v[r][4], v[r][5], v[r][6], v[r][7]), vlo, vhi);
-            if (e.w) atomicOr(err, ERR_BYTES);
-            l = e.x;
-            h = e.y;
-            n = e.z;
-        }
-        chunk[c] = make_uint4(l, h, n, 0u);
-    }
+    decode_chunks<kPackThreads>(cbase, nchunks, vbeg, vend, chunk, err);
     __syncthreads();
 
 #pragma unroll

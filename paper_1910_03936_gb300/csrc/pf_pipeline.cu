@@ -172,7 +172,7 @@ pf_status enqueue_chunk(Job &J, Slot &s, int64_t nc) {
     a.n = nc;
     a.err = ctx->d_err;
     a.dist = s.dist;  // E + 1 for the pairs the filter rejects
-    if (ctx->resolve_bounds && (J.dec & 3u) == 3u) a.need = s.scr.need;
+    if (ctx->resolve_bounds && (J.dec & 1u)) a.need = s.scr.need;
     cudaStream_t saved = ctx->stream;
     ctx->stream = s.st;
     pf_status st = ctx->run_filter(J.dec, a, s.scr);

@@ -178,6 +178,54 @@ def test_pack_neighbour_bytes_never_leak(pf, ctx):
             assert np.array_equal(got.cpu().numpy().view(np.uint32), want)
 
 
+@pytest.mark.parametrize("maxlen", [70, 255, 600])
+def test_pack_ragged_blocks_and_spare_words(pf, ctx, maxlen):
+    """The ragged layout with empty sequences, short and long sequences
+    from an unaligned start, bytes that are not bases before the first and
+    after the last sequence (never an error) and inside (packed as N, an
+    error), and a word_off with a spare word after some sequences (all N)."""
+    from gpu_util import to_dev
+    rng = np.random.default_rng(maxlen)
+    n = 700
+    lens = rng.integers(0, maxlen + 1, size=n)
+    lens[rng.choice(n, 20, replace=False)] = 0
+    pre, post = 13, 40
+    body = rng.choice(np.frombuffer(b"ACGTNacgtn", np.uint8), size=int(lens.sum()))
+    whole = np.concatenate([np.frombuffer(b"@" * pre, np.uint8), body,
+                            np.frombuffer(b"%" * post, np.uint8)])
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    words = (lens + 31) // 32
+    spare = (rng.random(n) < 0.1).astype(np.int64)
+    wo = np.concatenate([[0], np.cumsum(words + spare)]).astype(np.int64)
+    total = int(wo[-1])
+    for bad in (False, True):
+        src = whole.copy()
+        if bad:
+            pos = pre + rng.choice(len(body), 2, replace=False)
+            src[pos] = np.frombuffer(b"#-", np.uint8)
+        dev = to_dev(src)
+        out = pf.Seqs.empty(total, "cuda:0", word_off=to_dev(wo))
+        for t in (out.lo, out.hi, out.nmask):
+            t.fill_(0x5A5A5A5A)
+        pf.pf_pack(ctx, dev[1:], to_dev(off + pre - 1), to_dev(wo), out)
+        if bad:
+            with pytest.raises(pf.PFError):
+                pf.pf_sync(ctx)
+        else:
+            pf.pf_sync(ctx)
+        owo, lo, hi, nm, nbad = oracle.pack_batch(src[pre:pre + len(body)], off)
+        assert nbad == (2 if bad else 0)
+        got = [t.cpu().numpy()[:total].view(np.uint32) for t in (out.lo, out.hi, out.nmask)]
+        for s_ in range(n):
+            a, b = int(owo[s_]), int(owo[s_ + 1])
+            g = int(wo[s_])
+            for plane, want in zip(got, (lo, hi, nm)):
+                assert np.array_equal(plane[g:g + b - a], want[a:b]), (maxlen, s_)
+            if spare[s_]:
+                assert got[0][g + b - a] == 0 and got[1][g + b - a] == 0
+                assert got[2][g + b - a] == 0xFFFFFFFF
+
+
 @pytest.mark.parametrize("length,n", [(1, 5000), (2, 3001), (32, 2047), (150, 4000),
                                       (4000, 300), (131072, 3), (131073, 2)])
 def test_pack_fixed_across_tiles(pf, ctx, length, n):
@@ -439,7 +487,8 @@ def test_filter_verify_path(pf, ctx, case_data, name):
 
 @pytest.mark.parametrize("name", [c[0] for c in CASES])
 @pytest.mark.parametrize("small", [0, 1 << 30])
-def test_resolved_pairs_equal_full_verification(pf, ctx, case_data, name, small):
+@pytest.mark.parametrize("dec", [1, 3])
+def test_resolved_pairs_equal_full_verification(pf, ctx, case_data, name, small, dec):
     """Accepted pairs whose SneakySnake count equals their Hamming distance
     skip verification; their distances (and every other output) equal those
     of verifying every accepted pair, and the oracle's, through the
@@ -456,7 +505,7 @@ def test_resolved_pairs_equal_full_verification(pf, ctx, case_data, name, small)
             acc = torch.zeros(2 * n, dtype=torch.uint8, device="cuda:0")
             cnt = torch.zeros(2 * n, dtype=torch.int16, device="cuda:0")
             dist = torch.full((n,), -5, dtype=torch.int32, device="cuda:0")
-            pf.pf_filter_verify(ctx, 3, D.pairs, D.lens, D.E, D.E_max, acc, cnt, dist, n)
+            pf.pf_filter_verify(ctx, dec, D.pairs, D.lens, D.E, D.E_max, acc, cnt, dist, n)
             pf.pf_sync(ctx)
             outs.append((acc.cpu().numpy(), cnt.cpu().numpy(), dist.cpu().numpy()))
             counts.append(pf.pf_last_verified_count(ctx))
@@ -466,7 +515,9 @@ def test_resolved_pairs_equal_full_verification(pf, ctx, case_data, name, small)
     for x, y in zip(outs[0], outs[1]):
         assert np.array_equal(x, y)
     assert np.array_equal(outs[0][2], want)
-    assert np.array_equal(outs[0][0].reshape(2, n), oa)
+    slots = 2 if dec == 3 else 1
+    assert np.array_equal(outs[0][0][:slots * n].reshape(slots, n), oa[:slots])
+    assert np.array_equal(outs[0][1][:slots * n].reshape(slots, n), oc[:slots])
     ham = oracle.int_batch("hamming", P)
     resolved = (oa[0] == 1) & (oc[0] == ham)
     assert np.array_equal(outs[0][2][resolved], ham[resolved])
