@@ -161,7 +161,7 @@ pack_fixed_kernel(const uint8_t *ascii, int64_t nseq, int len, int W, uint32_t w
 // span at most kStreamWords + 1 chunks (from A = the buffer start rounded
 // down to 32 bytes), which the block decodes into shared memory first, then
 // cuts out its words.
-__global__ void __launch_bounds__(kPackThreads, 4)
+__global__ void __launch_bounds__(kPackThreads, 5)
 pack_stream_kernel(const uint8_t *ascii, int64_t nseq, int len, int W, uint32_t wmagic,
                    uint32_t *lo, uint32_t *hi, uint32_t *nm, unsigned *err) {
     __shared__ uint4 chunk[kStreamWords + 1];
