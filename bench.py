@@ -583,7 +583,7 @@ def main_gpu(args):
     # arrays that the tuner picks; pack_stream, one launch per 2M sequences,
     # two per pair; verify<u32> on the pairs left after equal bounds)
     traffic_per_pair = {"filter": (248.146432e6 + 11.001856e6) / 2e6,
-                        "pack": 2 * (300.083456e6 + 92.212992e6) / 2e6,
+                        "pack": 2 * (300.054784e6 + 91.782656e6) / 2e6,
                         "verify": (173.886208e6 + 5.08544e6) / 2e6}
     sm_mhz = clk.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
     alu_peak = 152 * 64 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # Top/s, ALU pipe
