@@ -18,21 +18,20 @@ constexpr int kPackThreads = 256;
 // plane over two chunk words.  A block decodes up to 4 chunks per thread,
 // two 16-byte loads each (coalesced across the warp, no re-reads).
 constexpr int kStreamChunksPerThread = 4;
-constexpr int kStreamChunks = kStreamChunksPerThread * kPackThreads;  // fixed layout
+constexpr int kStreamChunks = kStreamChunksPerThread * kPackThreads;
 constexpr int kStreamWords = kStreamChunks - 1;
 
 // Decode chunks [0, nchunks) from cbase (32-byte aligned) into chunk[].
 // Bytes of [vbeg, vend) are the sequences'; the 4-byte words that hold
 // them are read, others count as "NNNN"; a byte outside [vbeg, vend) that
 // is not a base never raises the error.
-template <int THREADS>
 __device__ __forceinline__ void decode_chunks(uintptr_t cbase, int nchunks, uintptr_t vbeg,
                                               uintptr_t vend, uint4 *chunk, unsigned *err) {
     const uintptr_t lo4 = vbeg & ~uintptr_t(3), hi4 = (vend + 3) & ~uintptr_t(3);
     uint32_t v[kStreamChunksPerThread][8];
 #pragma unroll
     for (int r = 0; r < kStreamChunksPerThread; ++r) {
-        const int c = threadIdx.x + r * THREADS;
+        const int c = threadIdx.x + r * kPackThreads;
         if (c >= nchunks) continue;
         const uintptr_t ca = cbase + 32 * (uintptr_t)c;
         if (ca >= lo4 && ca + 32 <= hi4) {
@@ -51,7 +50,7 @@ __device__ __forceinline__ void decode_chunks(uintptr_t cbase, int nchunks, uint
     }
 #pragma unroll
     for (int r = 0; r < kStreamChunksPerThread; ++r) {
-        const int c = threadIdx.x + r * THREADS;
+        const int c = threadIdx.x + r * kPackThreads;
         if (c >= nchunks) continue;
         uint32_t l, h, n;
         if (decode32(v[r], l, h, n)) {
@@ -189,7 +188,7 @@ pack_stream_kernel(const uint8_t *ascii, int64_t nseq, int len, int W, uint32_t 
     const uintptr_t cbase = A + 32 * (uintptr_t)s_j0;
     // the bytes of the buffer
     const uintptr_t vbeg = src, vend = src + (uintptr_t)(nseq * (int64_t)len);
-    decode_chunks<kPackThreads>(cbase, nchunks, vbeg, vend, chunk, err);
+    decode_chunks(cbase, nchunks, vbeg, vend, chunk, err);
     __syncthreads();
 
 #pragma unroll
