@@ -218,6 +218,55 @@ def serve_measure(pf, ctx, seconds_per_load, seed):
 # the other configurations (their own lines; the default line is the
 # 150 bp, E = 6 workload above)
 
+def run_threshold_sweep(args, pf, ctx, timed, dev):
+    """150 bp pairs at every threshold E = 0..15, one batch per E (the same
+    recipe as the headline batch, seed 0x5EED0002 + E): SneakySnake alone
+    batched (tuned) vs plain, and the step of both deciders with
+    verification.  One JSON line per E, then a summary line."""
+    import torch
+    import synth
+    n = args.pairs
+    W = (M + 31) // 32
+    rd = pf.Seqs.empty(n * W, dev, stride_words=W)
+    rf = pf.Seqs.empty(n * W, dev, stride_words=W)
+    pairs = pf.Pairs(rd, rf)
+    lens = torch.full((n,), M, dtype=torch.int32, device=dev)
+    acc = torch.empty(2 * n, dtype=torch.uint8, device=dev)
+    cnt = torch.empty(2 * n, dtype=torch.int16, device=dev)
+    dist = torch.empty(n, dtype=torch.int32, device=dev)
+    reps = max(1, args.steps)
+    rows = {}
+    for E in range(16):
+        P = synth.generate(synth.SKEWED, 0x5EED0002 + E, n, m=M, E=E, kmax=KMAX)
+        reads = torch.from_numpy(P.reads).to(dev)
+        refs = torch.from_numpy(P.refs).to(dev)
+        del P
+        Et = torch.full((n,), E, dtype=torch.int16, device=dev)
+        pack = lambda: (pf.pf_pack_fixed(ctx, reads, n, M, rd), pf.pf_pack_fixed(ctx, refs, n, M, rf))
+        pack()
+        tune_n = min(n, 2_000_000)
+        t1 = pf.pf_tune(ctx, 1, pairs, lens, E, n=tune_n, reps=2)
+        t3 = pf.pf_tune(ctx, 3, pairs, lens, E, n=tune_n, reps=2)
+        ss_b = timed(lambda: pf.pf_filter(ctx, 1, pairs, lens, None, E, acc, cnt, n), reps)
+        ss_p = timed(lambda: pf.pf_filter_plain(ctx, 1, pairs, lens, None, E, acc, cnt, n), reps)
+        step = timed(lambda: (pack(), pf.pf_filter_verify(ctx, 3, pairs, lens, Et, E, acc, cnt,
+                                                          dist, n)), reps)
+        n_ver = pf.pf_last_verified_count(ctx)
+        row = {"E": E, "pairs": n, "ss_batched_pairs_s": n / (ss_b / 1000.0),
+               "ss_plain_pairs_s": n / (ss_p / 1000.0), "batched_over_plain": ss_p / ss_b,
+               "tuned_cfg_ss": list(t1[:2]), "tuned_cfg_both": list(t3[:2]),
+               "step_ms": step, "step_pairs_s": n / (step / 1000.0),
+               "accepted_frac": float(acc[:n].float().mean().item()),
+               "verified_frac": n_ver / n}
+        rows[E] = row
+        print(json.dumps(row), flush=True)
+        del reads, refs
+    print(json.dumps({"workload": "cfg2_sweep", "read_len": M, "pairs_per_E": n,
+                      "step": "pack x2 + filter (both deciders) + compact + verify",
+                      "rows": rows}), flush=True)
+    pf.pf_destroy(ctx)
+
+
 def run_other_workload(args):
     import torch
     import synth
@@ -242,6 +291,9 @@ def run_other_workload(args):
         return a.elapsed_time(b) / reps
 
     w = args.workload
+    if w == "cfg2_sweep":
+        run_threshold_sweep(args, pf, ctx, timed, dev)
+        return
     if w == "cfg1":   # plain SneakySnake, 100k pairs of 100 bp from ASCII, E = 5
         P = synth.generate(synth.UNIFORM, 0x5EED0000, 100_000, m=100, E=5, kmax=20)
         fixed, Emax, kind = 100, 5, "uniform"
@@ -681,7 +733,8 @@ def main():
                     help="time one filter kernel instead of the step (profiling)")
     ap.add_argument("--deciders", type=int, default=3)
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--workload", default="headline", choices=["headline", "cfg1", "cfg3", "cfg4"],
+    ap.add_argument("--workload", default="headline",
+                    choices=["headline", "cfg1", "cfg3", "cfg4", "cfg2_sweep"],
                     help="other configurations, each on its own line")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     args = ap.parse_args()

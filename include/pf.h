@@ -207,8 +207,8 @@ PF_API pf_status pf_tune_batch(pf_ctx *ctx, unsigned deciders, const pf_pairs *p
  * plain one-thread-per-pair kernel serving E_max, no binning and no
  * per-threshold launches, whose fixed costs dominate small batches.
  * Default 2^20; 0 sends every batch of pf_filter / pf_filter_verify /
- * pf_run_host through the batched scheduler.  pf_tune always times the
- * batched scheduler.  PF_EINVAL for pairs < 0. */
+ * pf_run_host through the batched scheduler (unless pf_tune chose the
+ * plain kernel).  PF_EINVAL for pairs < 0. */
 PF_API pf_status pf_set_small_batch(pf_ctx *ctx, int64_t pairs);
 
 /* enable != 0 (the default): pf_filter_verify and pf_run_host with
@@ -223,14 +223,19 @@ PF_API pf_status pf_set_resolve_by_bounds(pf_ctx *ctx, int enable);
  * PF_EINVAL if cfg cannot serve E. */
 PF_API pf_status pf_tune_set(pf_ctx *ctx, unsigned deciders, int E, int cfg, int chunk);
 
-/* The configuration and chunk currently used for (deciders, E). */
+/* The configuration and chunk currently used for (deciders, E); cfg = -1
+ * when pf_tune chose the plain kernel. */
 PF_API pf_status pf_tune_get(pf_ctx *ctx, unsigned deciders, int E, int *cfg, int *chunk);
 
 /* Autotuner: time every configuration that serves E, with work chunks of
- * 64, 256 and 1024 pairs, on the n given pairs evaluated at threshold E
- * (CUDA events on the context's stream, best of `reps` runs each), keep
- * the fastest for (deciders, E) and report it (host outputs, may be NULL).
- * Synchronises the stream.  Allocates and frees its own output buffers. */
+ * 64, 256 and 1024 pairs, and the plain one-thread-per-pair kernel, on the
+ * n given pairs evaluated at threshold E (CUDA events on the context's
+ * stream, best of `reps` runs each), keep the fastest for (deciders, E) and
+ * report it (host outputs, may be NULL; *best_cfg = -1 for the plain
+ * kernel, chosen only when it beats the scheduler's best by 10%, which
+ * later batches then take whenever every threshold they can hold chose
+ * it).  Synchronises the stream.  Allocates and frees its own
+ * output buffers. */
 PF_API pf_status pf_tune(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs,
                          const int32_t *lens, int E, int64_t n, int reps,
                          int *best_cfg, int *best_chunk, float *best_ms);

@@ -494,7 +494,15 @@ static int plain_index(int E_max) {
 }
 
 pf_status pf_ctx::run_filter(unsigned dec, const FilterArgs &a, const Scratch &s) {
-    if (a.n < small_batch)  // fixed costs of binning and per-bin launches dominate
+    // small batches: fixed costs of binning and per-bin launches dominate;
+    // otherwise the plain kernel where pf_tune found it fastest for every
+    // threshold the batch can hold
+    bool plain = a.n < small_batch;
+    if (!plain) {
+        plain = true;
+        for (int e = a.E ? 0 : a.E_max; e <= a.E_max && plain; ++e) plain = tune_plain[dec][e];
+    }
+    if (plain)
         return cuda(launch_filter_plain((int)dec, plain_index(a.E_max), a, stream),
                     "filter launch");
     return run_batched(dec, a, s);
@@ -701,6 +709,7 @@ pf_status pf_tune_batch(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs,
         if (st == PF_OK) {
             ctx->tune_cfg[deciders][e] = bc;
             ctx->tune_chunk[deciders][e] = bk;
+            ctx->tune_plain[deciders][e] = false;
         }
     }
     cudaEventDestroy(e0);
@@ -725,6 +734,7 @@ pf_status pf_tune_set(pf_ctx *ctx, unsigned deciders, int E, int cfg, int chunk)
         return ctx->fail(PF_EINVAL, "pf_tune_set: bad deciders/E/cfg/chunk");
     ctx->tune_cfg[deciders][E] = cfg;
     ctx->tune_chunk[deciders][E] = chunk;
+    ctx->tune_plain[deciders][E] = false;
     return PF_OK;
 }
 
@@ -732,7 +742,7 @@ pf_status pf_tune_get(pf_ctx *ctx, unsigned deciders, int E, int *cfg, int *chun
     if (!ctx) return PF_EINVAL;
     if ((deciders & 3u) == 0 || (deciders & ~3u) || E < 0 || E > PF_MAX_E)
         return ctx->fail(PF_EINVAL, "pf_tune_get: bad deciders/E");
-    if (cfg) *cfg = ctx->tune_cfg[deciders][E];
+    if (cfg) *cfg = ctx->tune_plain[deciders][E] ? -1 : ctx->tune_cfg[deciders][E];
     if (chunk) *chunk = ctx->tune_chunk[deciders][E];
     return PF_OK;
 }
@@ -787,14 +797,37 @@ pf_status pf_tune(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs, const i
             }
         }
     }
+    // the plain one-thread-per-pair kernel over the same pairs
+    bool plain_best = false;
+    if (st == PF_OK) {
+        const FilterArgs a = make_filter_args(ctx, pairs, lens, nullptr, E, acc, cnt, n);
+        float best = 1e30f;
+        for (int r = 0; r <= reps && st == PF_OK; ++r) {  // first run warms up
+            cudaEventRecord(e0, ctx->stream);
+            st = ctx->cuda(launch_filter_plain((int)deciders, plain_index(E), a, ctx->stream),
+                           "tune launch");
+            cudaEventRecord(e1, ctx->stream);
+            if (st == PF_OK) st = ctx->cuda(cudaEventSynchronize(e1), "tune sync");
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (r > 0 && ms < best) best = ms;
+        }
+        // by a clear margin: the scheduler's fixed cost (one more launch)
+        // weighs more on a tuning sample than on the large batches it serves
+        if (st == PF_OK && best < 0.9f * bms) {
+            bms = best;
+            plain_best = true;
+        }
+    }
     ctx->tune_cfg[deciders][E] = (st == PF_OK) ? bc : keep_cfg;
     ctx->tune_chunk[deciders][E] = (st == PF_OK) ? bk : keep_chunk;
+    if (st == PF_OK) ctx->tune_plain[deciders][E] = plain_best;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(acc);
     cudaFree(cnt);
     if (st != PF_OK) return st;
-    if (best_cfg) *best_cfg = bc;
+    if (best_cfg) *best_cfg = plain_best ? -1 : bc;
     if (best_chunk) *best_chunk = bk;
     if (best_ms) *best_ms = bms;
     return PF_OK;

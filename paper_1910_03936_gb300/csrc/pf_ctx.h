@@ -46,6 +46,7 @@ struct pf_ctx {
 
     // tuned kernel per decider set and threshold
     int tune_cfg[4][PF_MAX_E + 1];
+    bool tune_plain[4][PF_MAX_E + 1] = {};  // pf_tune found the plain kernel fastest
     int tune_chunk[4][PF_MAX_E + 1];
     // batches of fewer pairs take one plain launch (no binning, no per-bin
     // launches); 0 sends every batch through the batched scheduler

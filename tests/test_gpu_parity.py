@@ -547,14 +547,41 @@ def test_two_phase_configs_on_ragged_pairs(pf, ctx, case_data):
 # ---- scheduler tuning ------------------------------------------------------------
 
 def test_tuner_picks_a_valid_config_and_stays_exact(pf, ctx, case_data):
+    """pf_tune keeps a configuration serving E (or -1, the plain kernel),
+    and the filter stays exact with it; the previous choice is restored so
+    that later tests keep exercising the scheduler's kernels."""
     from gpu_util import filter_dev
     P, D, (oa, oc) = case_data["cfg2_150bp_E6"]
-    cfg, chunk, ms = pf.pf_tune(ctx, 3, D.pairs, D.lens, 6, reps=1)
-    tpp, dpt, ecap, xe, words = pf.pf_kernel_configs()[cfg]
-    assert (xe == 6 or (xe < 0 and ecap >= 6)) and ms > 0 and chunk in (64, 256, 1024)
-    assert pf.pf_tune_get(ctx, 3, 6) == (cfg, chunk)
-    a, c = filter_dev(ctx, D, 3)
-    assert np.array_equal(c, oc) and np.array_equal(a, oa)
+    before = pf.pf_tune_get(ctx, 3, 6)
+    try:
+        cfg, chunk, ms = pf.pf_tune(ctx, 3, D.pairs, D.lens, 6, reps=1)
+        assert ms > 0 and chunk in (64, 256, 1024)
+        if cfg != -1:
+            tpp, dpt, ecap, xe, words = pf.pf_kernel_configs()[cfg]
+            assert xe == 6 or (xe < 0 and ecap >= 6)
+        assert pf.pf_tune_get(ctx, 3, 6) == (cfg, chunk)
+        a, c = filter_dev(ctx, D, 3)
+        assert np.array_equal(c, oc) and np.array_equal(a, oa)
+    finally:
+        pf.pf_tune_set(ctx, 3, 6, *before)
+    assert pf.pf_tune_get(ctx, 3, 6) == before
+
+
+def test_tuner_can_choose_the_plain_kernel(pf, ctx, case_data):
+    """At E = 0 (one diagonal, a memory-bound filter) the plain kernel is
+    timed too; whatever wins, pf_filter routes uniform-E batches to it and
+    stays exact, and pf_tune_set returns the threshold to the scheduler."""
+    from gpu_util import filter_dev
+    P, D, (oa, oc) = case_data["cfg2_150bp_E0"]
+    before = pf.pf_tune_get(ctx, 1, 0)
+    try:
+        cfg, chunk, ms = pf.pf_tune(ctx, 1, D.pairs, D.lens, 0, reps=1)
+        assert pf.pf_tune_get(ctx, 1, 0)[0] == cfg
+        a, c = filter_dev(ctx, D, 1)
+        assert np.array_equal(c, oc[[0]]) and np.array_equal(a, oa[[0]])
+    finally:
+        pf.pf_tune_set(ctx, 1, 0, *before)
+    assert pf.pf_tune_get(ctx, 1, 0) == before
 
 
 def test_tune_batch_tunes_each_threshold_on_its_own_pairs(pf, ctx, case_data):
