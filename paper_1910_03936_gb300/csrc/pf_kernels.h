@@ -34,9 +34,12 @@ constexpr KernelCfg kBatchCfgs[] = {
     {1, 6, 5, 5, 8},     {1, 7, 6, 6, 8},     {1, 8, 7, 7, 7},     {1, 9, 8, 8, 6},
     {1, 10, 9, 9, 5},    {1, 11, 10, 10, 5},  {1, 12, 11, 11, 4},  {1, 13, 12, 12, 4},
     // and with 5-word arrays (pairs up to 160 bases) for E = 1..7: smaller
-    // blocks, more of them per SM
+    // blocks, more of them per SM,
     {1, 2, 1, 1, 5},     {1, 3, 2, 2, 5},     {1, 4, 3, 3, 5},     {1, 5, 4, 4, 5},
     {1, 6, 5, 5, 5},     {1, 7, 6, 6, 5},     {1, 8, 7, 7, 5},
+    // and for E = 11..15 (up to 79 KB per block, two or three per SM)
+    {1, 12, 11, 11, 5},  {1, 13, 12, 12, 5},  {1, 14, 13, 13, 5},  {1, 15, 14, 14, 5},
+    {1, 16, 15, 15, 5},
 };
 
 // The two-phase form applies where SneakySnake runs (deciders 1 and 3);
