@@ -219,8 +219,8 @@ PF_API pf_status pf_set_small_batch(pf_ctx *ctx, int64_t pairs);
 PF_API pf_status pf_set_resolve_by_bounds(pf_ctx *ctx, int enable);
 
 /* Use configuration cfg and a work chunk of `chunk` pairs (1..65536) for
- * threshold E under decider set `deciders` in later pf_filter calls.
- * PF_EINVAL if cfg cannot serve E. */
+ * threshold E under decider set `deciders` in later pf_filter calls; cfg =
+ * -1 selects the plain kernel.  PF_EINVAL if cfg cannot serve E. */
 PF_API pf_status pf_tune_set(pf_ctx *ctx, unsigned deciders, int E, int cfg, int chunk);
 
 /* The configuration and chunk currently used for (deciders, E); cfg = -1
@@ -232,9 +232,9 @@ PF_API pf_status pf_tune_get(pf_ctx *ctx, unsigned deciders, int E, int *cfg, in
  * n given pairs evaluated at threshold E (CUDA events on the context's
  * stream, best of `reps` runs each), keep the fastest for (deciders, E) and
  * report it (host outputs, may be NULL; *best_cfg = -1 for the plain
- * kernel, chosen only when it beats the scheduler's best by 10%, which
- * later batches then take whenever every threshold they can hold chose
- * it).  Synchronises the stream.  Allocates and frees its own
+ * kernel, which later batches take whenever every threshold they can hold
+ * chose it).  The plain kernel is the default at E = 0 (one diagonal, bound
+ * by memory); a measurement replaces a default only by a 10% margin.  Synchronises the stream.  Allocates and frees its own
  * output buffers. */
 PF_API pf_status pf_tune(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs,
                          const int32_t *lens, int E, int64_t n, int reps,

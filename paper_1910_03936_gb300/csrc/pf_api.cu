@@ -205,11 +205,16 @@ int pf::pf_default_cfg(int E) {
     return -1;
 }
 
+// E = 0 compares one diagonal and is bound by memory: the plain kernel
+// (full occupancy, no shared work counter) is the default there.
+static bool default_plain(int E) { return E == 0; }
+
 void pf_ctx::reset_tuning() {
     for (int d = 0; d < 4; ++d)
         for (int e = 0; e <= PF_MAX_E; ++e) {
             tune_cfg[d][e] = pf_default_cfg(e);
             tune_chunk[d][e] = 256;
+            tune_plain[d][e] = default_plain(e);
         }
 }
 
@@ -729,12 +734,13 @@ pf_status pf_set_small_batch(pf_ctx *ctx, int64_t pairs) {
 
 pf_status pf_tune_set(pf_ctx *ctx, unsigned deciders, int E, int cfg, int chunk) {
     if (!ctx) return PF_EINVAL;
-    if ((deciders & 3u) == 0 || (deciders & ~3u) || E < 0 || E > PF_MAX_E || cfg < 0 ||
-        cfg >= kNumBatchCfgs || !cfg_serves(kBatchCfgs[cfg], E) || chunk < 1 || chunk > 65536)
+    if ((deciders & 3u) == 0 || (deciders & ~3u) || E < 0 || E > PF_MAX_E || cfg < -1 ||
+        cfg >= kNumBatchCfgs || (cfg >= 0 && !cfg_serves(kBatchCfgs[cfg], E)) || chunk < 1 ||
+        chunk > 65536)
         return ctx->fail(PF_EINVAL, "pf_tune_set: bad deciders/E/cfg/chunk");
-    ctx->tune_cfg[deciders][E] = cfg;
+    ctx->tune_plain[deciders][E] = cfg == -1;  // -1: the plain kernel
+    if (cfg >= 0) ctx->tune_cfg[deciders][E] = cfg;
     ctx->tune_chunk[deciders][E] = chunk;
-    ctx->tune_plain[deciders][E] = false;
     return PF_OK;
 }
 
@@ -812,9 +818,11 @@ pf_status pf_tune(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs, const i
             cudaEventElapsedTime(&ms, e0, e1);
             if (r > 0 && ms < best) best = ms;
         }
-        // by a clear margin: the scheduler's fixed cost (one more launch)
-        // weighs more on a tuning sample than on the large batches it serves
-        if (st == PF_OK && best < 0.9f * bms) {
+        // a change from the default by a clear margin only: a tuning sample
+        // weighs the scheduler's fixed cost (one more launch) more than the
+        // large batches it serves, and keeps part of its input in L2
+        const float margin = default_plain(E) ? 1.1f : 0.9f;
+        if (st == PF_OK && best < margin * bms) {
             bms = best;
             plain_best = true;
         }

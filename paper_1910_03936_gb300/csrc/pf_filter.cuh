@@ -562,7 +562,7 @@ __device__ __forceinline__ void filter_split_pair(const FilterArgs &a, int64_t p
 // Up to E = 7 the registers are held to five blocks per SM (with 5-word
 // arrays the shared memory allows them too).
 template <int DEC, int XE, int WMAX>
-__global__ void __launch_bounds__(kSplitWarps * 32, (XE <= 7 ? 5 : 3))
+__global__ void __launch_bounds__(kSplitWarps * 32, (XE <= 7 ? 5 : (XE <= 10 ? 4 : 3)))
     filter_split_kernel(BatchArgs b, int bin) {
     extern __shared__ uint32_t split_maps[];
     constexpr int NS = 2 * XE + 1;

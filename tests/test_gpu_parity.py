@@ -608,6 +608,12 @@ def test_tuner_can_choose_the_plain_kernel(pf, ctx, case_data):
         assert pf.pf_tune_get(ctx, 1, 0)[0] == cfg
         a, c = filter_dev(ctx, D, 1)
         assert np.array_equal(c, oc[[0]]) and np.array_equal(a, oa[[0]])
+        pf.pf_tune_set(ctx, 1, 0, -1, 64)  # the plain kernel, by hand
+        assert pf.pf_tune_get(ctx, 1, 0) == (-1, 64)
+        a, c = filter_dev(ctx, D, 1)
+        assert np.array_equal(c, oc[[0]]) and np.array_equal(a, oa[[0]])
+        with pytest.raises(pf.PFError):
+            pf.pf_tune_set(ctx, 1, 0, -2, 64)
     finally:
         pf.pf_tune_set(ctx, 1, 0, *before)
     assert pf.pf_tune_get(ctx, 1, 0) == before
