@@ -127,7 +127,7 @@ pf_status pf_ctx::cuda(cudaError_t e, const char *what) {
 
 pf_status pf_ctx::ensure_scratch(size_t bytes) {
     if (bytes <= scratch_bytes) return PF_OK;
-    verified_valid = false;
+    verified_state = 0;
     if (scratch) {
         cudaStreamSynchronize(stream);
         cudaFree(scratch);
@@ -569,7 +569,12 @@ pf_status pf_filter_verify(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs
                            const int32_t *lens, const int16_t *E, int E_max, uint8_t *accept,
                            int16_t *count, int32_t *dist, int64_t n) {
     pf_status st = check_filter_args(ctx, deciders, pairs, lens, E_max, accept, count, n);
-    if (st != PF_OK || n == 0) return st;
+    if (st != PF_OK) return st;
+    ctx->verified_state = 0;
+    if (n == 0) {
+        ctx->verified_state = 2;
+        return PF_OK;
+    }
     if (!dist) return ctx->fail(PF_EINVAL, "null pointer argument");
     cudaSetDevice(ctx->device);
     Scratch s;
@@ -591,14 +596,18 @@ pf_status pf_filter_verify(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs
     st = ctx->cuda(launch_verify(to_view(pairs), lens, E, E_max, s.idx, s.n_idx, n, dist,
                                  ctx->d_err, ctx->sms, ctx->stream),
                    "verify launch");
-    ctx->verified_valid = st == PF_OK;
+    ctx->verified_state = (st == PF_OK) ? 1 : 0;
     return st;
 }
 
 pf_status pf_last_verified_count(pf_ctx *ctx, int64_t *n_verified) {
     if (!ctx) return PF_EINVAL;
     if (!n_verified) return ctx->fail(PF_EINVAL, "null pointer argument");
-    if (!ctx->verified_valid || !ctx->scratch)
+    if (ctx->verified_state == 2) {
+        *n_verified = 0;
+        return PF_OK;
+    }
+    if (ctx->verified_state != 1 || !ctx->scratch)
         return ctx->fail(PF_EINVAL, "no pf_filter_verify result on this context");
     cudaSetDevice(ctx->device);
     pf_status st = ctx->cuda(cudaMemcpyAsync(n_verified, ctx->scratch, sizeof(int64_t),

@@ -52,7 +52,9 @@ struct pf_ctx {
     // launches); 0 sends every batch through the batched scheduler
     int64_t small_batch = int64_t(1) << 20;
     bool resolve_bounds = true;  // skip verifying pairs whose count bounds agree
-    bool verified_valid = false; // scratch holds the last pf_filter_verify's count
+    // what pf_last_verified_count reads: 0 nothing, 1 the count at the start
+    // of scratch, 2 zero (the last pf_filter_verify had no pairs)
+    int verified_state = 0;
     int grid_cache[4][pf::kNumBatchCfgs] = {};
 
     cudaStream_t side_streams[pf::kSideStreams] = {};

@@ -524,6 +524,17 @@ def test_resolved_pairs_equal_full_verification(pf, ctx, case_data, name, small,
     assert counts == [int(oa[0].sum() - resolved.sum()), int(oa[0].sum())]
 
 
+def test_last_verified_count_after_an_empty_batch(pf, ctx, case_data):
+    P, D, _ = case_data["cfg2_150bp_E6"]
+    acc = torch.zeros(2 * D.n, dtype=torch.uint8, device="cuda:0")
+    cnt = torch.zeros(2 * D.n, dtype=torch.int16, device="cuda:0")
+    dist = torch.zeros(D.n, dtype=torch.int32, device="cuda:0")
+    pf.pf_filter_verify(ctx, 3, D.pairs, D.lens, D.E, D.E_max, acc, cnt, dist, D.n)
+    assert pf.pf_last_verified_count(ctx) > 0
+    pf.pf_filter_verify(ctx, 3, D.pairs, D.lens, D.E, D.E_max, acc, cnt, dist, 0)
+    assert pf.pf_last_verified_count(ctx) == 0
+
+
 def test_two_phase_configs_on_ragged_pairs(pf, ctx, case_data):
     """The two-phase kernels on mixed lengths and thresholds: pairs longer
     than their shared arrays take the fused loop in the same warps."""
