@@ -373,12 +373,13 @@ struct PairFilter {
 };
 
 // h: the Hamming count (the d = 0 diagonal's mismatches), exact whenever
-// it is <= E and SneakySnake accepts (every word is then processed).  SneakySnake's obstacle count never exceeds the edit
-// distance within the band (each edit of a banded alignment costs the snake
-// at most one obstacle, and the greedy walk needs the fewest, Ch. 8), and the
-// Hamming distance never falls below it (substitutions alone align the
-// pair on d = 0).  When the two agree the distance is known: with a.need set
-// such a pair is written here and left out of verification.
+// it is <= E and SneakySnake accepts (every word is then processed).
+// SneakySnake's obstacle count never exceeds the edit distance within the
+// band (each edit of a banded alignment costs the snake at most one
+// obstacle, and the greedy walk needs the fewest, Ch. 8), and the Hamming
+// distance never falls below it (substitutions alone align the pair on
+// d = 0).  When the two agree the distance is known: with a.need set such a
+// pair is written here and left out of verification.
 template <int DEC>
 __device__ __forceinline__ void write_outputs(const FilterArgs &a, int64_t p, int E, int ssc,
                                               int gkc, int h) {
