@@ -142,8 +142,10 @@ PF_API pf_status pf_pack_layout(const int64_t *byte_off_host, int64_t nseq,
  * device int64[nseq+1] (sequence s occupies bytes [byte_off[s],
  * byte_off[s+1]) and words [word_off[s], word_off[s+1]) of each plane);
  * lo/hi/nmask: caller-allocated device planes of word_off[nseq] words.
- * Bytes other than A/C/G/T/N (either case) pack as N and raise PF_EDATA
- * at the next pf_sync. */
+ * Bits past a sequence's end in its last word, and any words a word_off
+ * leaves beyond ceil(len/32), are N.  Bytes other than A/C/G/T/N (either
+ * case) inside a sequence pack as N and raise PF_EDATA at the next
+ * pf_sync; bytes outside every sequence never change a plane or raise it. */
 PF_API pf_status pf_pack(pf_ctx *ctx, const uint8_t *ascii, const int64_t *byte_off,
                   const int64_t *word_off, int64_t nseq,
                   uint32_t *lo, uint32_t *hi, uint32_t *nmask);
