@@ -121,6 +121,15 @@ def max_over_ranks(value, dist=None):
     return float(t.item())
 
 
+def headline_config(n):
+    """The workload both arms name (the reference arm times a sample of it)."""
+    return {"workload": WORKLOAD, "pairs_per_gpu": n, "read_len": M, "E": E_HEAD,
+            "deciders": "SneakySnake+GateKeeper",
+            "verify": "SneakySnake accepts whose count differs from their Hamming "
+                      "distance (equal bounds resolve the rest)",
+            "l2": "inputs larger than L2 (9 GB resident)"}
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle baseline (also the reference arm)
 
@@ -160,11 +169,13 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "pairs": N_PAIRS, "read_len": M, "E": E_HEAD,
-                   "l2": "inputs larger than L2"},
+        "config": headline_config(args.pairs),
+        "sample_pairs_per_step": n_sample,
         "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": thr, "kind": "oracle",
-                         "sample": "pairs 0..%d of the workload per step (filter both "
-                                   "deciders + banded WF on SneakySnake accepts)" % n_sample},
+                         "sample": "each step times pairs 0..%d of the %d-pair workload "
+                                   "(filter both deciders + banded WF on SneakySnake "
+                                   "accepts); value = sampled pairs / time"
+                                   % (n_sample, args.pairs)},
         "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -612,9 +623,9 @@ def main_gpu(args):
     pk, pk_kind = peaks()
     stages = {"pack": pack_ms, "filter": filt_ms, "compact": compact_ms, "verify": verify_ms}
     dominant = max(stages, key=stages.get)
-    # Algorithmic work per launch (the per-unit figures of the method, see
-    # the design doc): bytes the stage must move, and integer operations of the
-    # method counted for every word of every pair (no early exit).
+    # Algorithmic work per launch (the per-unit figures of the method): bytes
+    # the stage must move, and integer operations of the method counted for
+    # every word of every pair (no early exit).
     D, Wd = 2 * E_HEAD + 1, (M + 31) // 32
     ops_filter = 5 * D * Wd + (8 * D * Wd + Wd) + (E_HEAD + 1) * (3 * D + 1)
     alg_bytes = {
@@ -665,11 +676,7 @@ def main_gpu(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "pairs_per_gpu": n, "read_len": M, "E": E_HEAD,
-                   "deciders": "SneakySnake+GateKeeper",
-                   "verify": "SneakySnake accepts whose count differs from their Hamming "
-                             "distance (equal bounds resolve the rest)",
-                   "l2": "inputs larger than L2 (9 GB resident)"},
+        "config": headline_config(n),
         "stages_ms": {"pack": pack_ms, "filter_compact_verify": fv_ms, "filter": filt_ms,
                       "compact": compact_ms, "verify": verify_ms,
                       "verify_every_accepted_pair": verify_accepted_ms,
@@ -699,10 +706,14 @@ def main_gpu(args):
     line["gpu_launches"] = args.steps * (2 + (1 if n_cfg == 1 else 4) + n_cfg + 3 + 1)
     if rank == 0 and world == 1 and not args.no_cpu:
         r, dt, thr = oracle_step_rate(args.cpu_sample)
+        r1, dt1, _ = oracle_step_rate(args.cpu_sample_1t, threads=1)
         line["cpu_baseline"] = {"value": r, "unit": "pairs/s", "cores": thr, "kind": "oracle",
                                 "sample": "first %d pairs of the workload (filter both "
                                           "deciders + banded WF on SneakySnake accepts), "
-                                          "%.1f s" % (args.cpu_sample, dt)}
+                                          "%.1f s" % (args.cpu_sample, dt),
+                                "single_thread": {"value": r1, "unit": "pairs/s", "cores": 1,
+                                                  "sample": "first %d pairs, %.1f s"
+                                                            % (args.cpu_sample_1t, dt1)}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     pf.pf_destroy(ctx)
@@ -719,6 +730,8 @@ def main():
     ap.add_argument("--pairs", type=int, default=N_PAIRS)
     ap.add_argument("--cpu-sample", type=int, default=8_000_000,
                     help="pairs of the oracle's timed sample for cpu_baseline (about 10 s)")
+    ap.add_argument("--cpu-sample-1t", type=int, default=300_000,
+                    help="pairs of the single-thread oracle sample (about 5 s)")
     ap.add_argument("--ref-sample", type=int, default=400_000,
                     help="pairs per step of --impl reference (K + W steps in a few minutes)")
     ap.add_argument("--no-cpu", action="store_true")

@@ -250,20 +250,24 @@ PF_API pf_status pf_compact(pf_ctx *ctx, const uint8_t *flags, int64_t n,
                      int64_t *idx, int64_t *n_out);
 
 /* Compaction that allocates nothing, for callers that cannot allocate
- * device memory (a stream under CUDA graph capture, a framework whose own
- * allocator owns all device memory, a path that cannot afford cudaMalloc's
- * implicit synchronisation).  The thesis has no counterpart: this is an
- * interface convenience.  Same result as pf_compact, but no context is
- * needed and the per-tile counters live in a fixed 256 KiB device array of
- * the library instead of context scratch:
+ * device memory: a framework whose own allocator owns every byte of device
+ * memory, or a latency path that cannot take cudaMalloc's implicit device
+ * synchronisation.  The thesis has no counterpart: this is an interface
+ * convenience.  Same result as pf_compact, but no context is needed and the
+ * per-tile counters live in a fixed 256 KiB device array of the library
+ * instead of context scratch:
  *   flags, idx, n_out  as in pf_compact (device pointers)
  *   stream             cudaStream_t to launch on (NULL = legacy default)
+ * The current device must own flags, idx, n_out and the stream.
  * n must be <= 134,217,728; larger n returns PF_EINVAL and launches nothing.
  * PF_ECUDA if a launch fails.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress), so make it before any
- * stream capture.  Every call shares the array: calls whose kernels overlap
- * on the GPU (other streams, other threads) race and must be serialised by
- * the caller.  Every GPU that loads the library holds the array until the
+ * array's device address (cudaGetSymbolAddress) and keeps it for the life
+ * of the process, so make that call before any stream capture, and do not
+ * call this function again after a cudaDeviceReset (or any other teardown of
+ * the device's primary context) in the same process: the kept address would
+ * be stale.  Every call shares the array: calls whose kernels overlap on the
+ * GPU (other streams, other threads) race and must be serialised by the
+ * caller.  Every GPU that loads the library holds the array until the
  * process exits. */
 PF_API pf_status pf_compact_noalloc(const uint8_t *flags, int64_t n, int64_t *idx,
                                     int64_t *n_out, void *stream);

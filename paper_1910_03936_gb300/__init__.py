@@ -329,26 +329,36 @@ def pf_filter_shd(ctx, pairs, lens, E, E_max, flags, accept, count, n=None):
                   count, n)
 
 
-def pf_compact(ctx, flags, idx, n_out, n=None):
+def _compact_args(flags, idx, n_out, n):
     _dt(flags, torch.uint8, "flags")
     _dt(idx, torch.int64, "idx")
     _dt(n_out, torch.int64, "n_out")
-    n = flags.numel() if n is None else n
+    n = flags.numel() if n is None else int(n)
+    if n < 0 or n > flags.numel() or n > idx.numel() or n_out.numel() < 1:
+        raise ValueError("n = %d outside the buffers (flags %d, idx %d, n_out %d elements)"
+                         % (n, flags.numel(), idx.numel(), n_out.numel()))
+    if not (flags.device == idx.device == n_out.device):
+        raise ValueError("flags, idx and n_out must be on one device")
+    return n
+
+
+def pf_compact(ctx, flags, idx, n_out, n=None):
+    n = _compact_args(flags, idx, n_out, n)
     _cur_stream(ctx)
-    _check(load().pf_compact(ctx.handle, _p(flags), int(n), _p(idx), _p(n_out)), ctx.handle)
+    _check(load().pf_compact(ctx.handle, _p(flags), n, _p(idx), _p(n_out)), ctx.handle)
 
 
 def pf_compact_noalloc(flags, idx, n_out, n=None, stream=None):
     """pf_compact without a context and without any device allocation
-    (fixed in-library counters, n <= 134,217,728; concurrent calls race)."""
-    _dt(flags, torch.uint8, "flags")
-    _dt(idx, torch.int64, "idx")
-    _dt(n_out, torch.int64, "n_out")
-    n = flags.numel() if n is None else n
-    if stream is None:
-        stream = torch.cuda.current_stream(flags.device).cuda_stream
-    _check(load().pf_compact_noalloc(_p(flags), int(n), _p(idx), _p(n_out),
-                                     ctypes.c_void_p(int(stream))))
+    (fixed in-library counters, n <= 134,217,728; concurrent calls race).
+    Runs with the buffers' device current, on its current stream unless
+    ``stream`` is given."""
+    n = _compact_args(flags, idx, n_out, n)
+    with torch.cuda.device(flags.device):
+        if stream is None:
+            stream = torch.cuda.current_stream(flags.device).cuda_stream
+        _check(load().pf_compact_noalloc(_p(flags), n, _p(idx), _p(n_out),
+                                         ctypes.c_void_p(int(stream))))
 
 
 def pf_verify(ctx, pairs, lens, E, E_max, idx, n_idx, dist, n=None):

@@ -1,13 +1,12 @@
 // Compaction for callers that cannot allocate device memory.
 //
 // pf_compact() takes its per-tile counters from scratch that the context
-// allocates with cudaMalloc.  Some callers cannot allocate at all: code that
-// runs while a stream is being captured into a CUDA graph (cudaMalloc is
-// not a stream operation and breaks the capture), code inside a framework
-// whose own allocator owns every byte of device memory, or a latency path
-// that cannot afford cudaMalloc's implicit device synchronisation.  For
-// them, pf_compact_noalloc() runs the same three kernels with the tile
-// counters in the fixed device array below, and allocates nothing.
+// allocates with cudaMalloc.  Some callers cannot allocate at all: code
+// inside a framework whose own allocator owns every byte of device memory,
+// or a latency path that cannot afford cudaMalloc's implicit device
+// synchronisation.  For them, pf_compact_noalloc() runs the same three
+// kernels with the tile counters in the fixed device array below, and
+// allocates nothing.
 #include <mutex>
 
 #include "pf_kernels.h"
@@ -28,7 +27,10 @@ int64_t *g_addr[kMaxDevices] = {};
 
 // Device address of g_noalloc_tiles on the current device.  In host code the
 // array's name is only a host-side stand-in, so the address comes from
-// cudaGetSymbolAddress, once per device, with that device current.
+// cudaGetSymbolAddress, once per device, with that device current.  The
+// address is kept for the life of the process: after a cudaDeviceReset the
+// module is loaded again and the kept address may be stale (the header tells
+// callers not to use this entry point across a reset).
 cudaError_t tiles_on_device(int64_t **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);

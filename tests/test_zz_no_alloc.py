@@ -1,5 +1,6 @@
 """pf_compact_noalloc: compaction for callers that cannot allocate device
-memory (graph capture, a framework-owned allocator, no implicit syncs).
+memory (a framework-owned allocator, a path that cannot take cudaMalloc's
+implicit synchronisation).
 
 It must give exactly what pf_compact gives, call after call, although its
 counters live in one fixed device array shared by every call.  This file
@@ -50,10 +51,19 @@ def test_noalloc_matches_pf_compact_twice(pf):
 
 
 def test_noalloc_rejects_sizes_beyond_its_array(pf):
+    # buffers really hold n elements, so that a regression of the host-side
+    # size check shows up as a wrong status or result, never as an access
+    # outside a buffer
     n = 134_217_728 + 1
-    f = torch.zeros(1, dtype=torch.uint8, device="cuda:0")
-    idx = torch.zeros(1, dtype=torch.int64, device="cuda:0")
-    k = torch.zeros(1, dtype=torch.int64, device="cuda:0")
+    f = torch.zeros(n, dtype=torch.uint8, device="cuda:0")
+    f[::1000] = 1
+    idx = torch.full((n,), -5, dtype=torch.int64, device="cuda:0")
+    k = torch.full((1,), -3, dtype=torch.int64, device="cuda:0")
     with pytest.raises(pf.PFError) as ei:
         pf.pf_compact_noalloc(f, idx, k, n)   # rejected on the host, nothing launched
     assert ei.value.status == 1
+    torch.cuda.synchronize()
+    assert int(k.item()) == -3                 # nothing was written
+    assert bool((idx[:1000] == -5).all()) and bool((idx[-1000:] == -5).all())
+    del f, idx
+    torch.cuda.empty_cache()
