@@ -177,3 +177,24 @@ def test_full_size_sampled(pf, ctx):
         want = oracle.int_batch(kind, sub, p0=p[0], p1=p[1])
         assert np.array_equal(cnt.cpu().numpy()[idx], want)
         assert np.array_equal(acc.cpu().numpy()[idx], (want <= 6).astype(np.uint8))
+
+
+def test_false_reject_examples_on_the_gpu(pf, ctx, golden):
+    # the hand-traced pairs that GateKeeper and Shouji reject although their
+    # edit distance is within E: the kernels reproduce those counts, and
+    # SneakySnake and the verifier accept them with their distance
+    from gpu_util import filter_dev, verify_dev
+    for name, slot in (("gatekeeper_false_reject.txt", "gk"), ("shouji_false_reject.txt", "sh")):
+        kv, _ = golden(name)
+        E = int(kv["E"])
+        reads = np.frombuffer(kv["read"].encode(), np.uint8)[None, :]
+        refs = np.frombuffer(kv["ref"].encode(), np.uint8)[None, :]
+        D = DevicePairs(ctx, ArrayPairs(reads, refs, E), fixed=reads.shape[1])
+        acc, cnt = filter_dev(ctx, D, 3)
+        assert cnt[0, 0] <= int(kv["edit_distance"]) and acc[0, 0] == 1
+        if slot == "gk":
+            assert cnt[1, 0] == int(kv["count"]) and acc[1, 0] == 0
+        else:
+            a, c = run(pf, ctx, pf.pf_filter_shouji, D)
+            assert c[0] == int(kv["count"]) and a[0] == 0
+        assert verify_dev(ctx, D)[0] == int(kv["edit_distance"])

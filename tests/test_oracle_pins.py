@@ -499,3 +499,56 @@ def test_shd_vacant_zero_closed_form():
         assert oracle.gatekeeper(read, ref, E) == E + 1
         # one streak of m - 2E ones
         assert oracle.gatekeeper_shd(read, ref, E, True, True) == min((m - 2 * E + 2) // 3, E + 1)
+
+
+# ---- false rejects of GateKeeper and Shouji: hand-traced minimal pairs -------
+
+def _bits(s):
+    return [int(c) for c in s]
+
+
+def test_gatekeeper_false_reject_example():
+    kv, _ = read_golden("gatekeeper_false_reject.txt")
+    read, ref, E = kv["read"], kv["ref"], int(kv["E"])
+    # the map's rows (d = -E..E) and their amends, as traced by hand
+    mp = oracle.neighborhood_map(read, ref, E)
+    for d in range(-E, E + 1):
+        assert mp[d + E].tolist() == _bits(kv["mask_d%d" % d]), d
+    assert mp[E].tolist() == _bits(kv["hamming_mask"])
+    anded = np.ones(len(read), dtype=np.uint8)
+    for d in range(-E, E + 1):
+        anded &= oracle.amend(mp[d + E])
+    assert anded.tolist() == _bits(kv["and_of_amended"])
+    assert oracle.gatekeeper(read, ref, E) == int(kv["count"])
+    assert oracle.wf(read, ref) == int(kv["edit_distance"]) <= E
+    # SneakySnake accepts it (its count never exceeds the edit distance)
+    assert oracle.sneakysnake(read, ref, E) <= int(kv["edit_distance"])
+
+
+def test_shouji_false_reject_example():
+    kv, _ = read_golden("shouji_false_reject.txt")
+    read, ref, E = kv["read"], kv["ref"], int(kv["E"])
+    mp = oracle.neighborhood_map(read, ref, E)
+    for d in range(-E, E + 1):
+        assert mp[d + E].tolist() == _bits(kv["map_d%d" % d]), d
+    v, ones = oracle.shouji_vector(read, ref, E)
+    assert v.tolist() == _bits(kv["bit_vector"])
+    assert ones == int(kv["count"]) and oracle.shouji(read, ref, E) == int(kv["count"])
+    assert oracle.wf(read, ref) == int(kv["edit_distance"]) <= E
+    assert oracle.sneakysnake(read, ref, E) <= int(kv["edit_distance"])
+
+
+@pytest.mark.parametrize("kind,L,E_first", [("gatekeeper", 4, 2), ("shouji", 6, 2)])
+def test_false_reject_examples_are_the_shortest(kind, L, E_first):
+    # every shorter pair over {A,C,G,T}, at every E, is accepted whenever its
+    # edit distance is within E, and at length L none is rejected below E_first
+    for length in range(1, L + 1):
+        for E in range(0, length if length < L else E_first):
+            reads, refs = all_pairs("ACGT", length)
+            P = ArrayPairs(reads, refs, E)
+            ed = oracle.int_batch("wf_banded", P)
+            if kind == "gatekeeper":
+                c = oracle.filter_batch(P, deciders=2)[1][0]
+            else:
+                c = oracle.int_batch("shouji", P)
+            assert not np.any((ed <= E) & (c > E)), (length, E)
