@@ -185,43 +185,136 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # serving: offered-load replay through the device-resident loop
 
-def serve_measure(pf, ctx, seconds_per_load, seed):
+def serve_pool(pf, seed, count=48, pinned=True):
     """Requests of log-uniform size in [1e3, 2e5] pairs, lengths uniform over
     {100, 150, 250}, E = round(r * len) with r ~ U[0, 0.10), 20/80 mix of
-    pairs within / beyond E (the serving recipe of synth).  Peak = pairs/s of
-    a burst of every request at once; then Poisson arrivals at 25/50/90% of
-    that peak.  Latency = submit to results in host memory."""
-    import torch
+    pairs within / beyond E (the serving recipe of synth), in page-locked
+    host memory."""
     import synth
     rng = np.random.default_rng(seed)
-    sizes = np.exp(rng.uniform(np.log(1e3), np.log(2e5), size=48)).astype(np.int64)
-    pool, keep, p0 = [], [], 0
+    sizes = np.exp(rng.uniform(np.log(1e3), np.log(2e5), size=count)).astype(np.int64)
+    pool, p0 = [], 0
     for n in sizes:
         P = synth.generate(synth.SERVE, seed, int(n), kmax=60, p0=p0)
         p0 += int(n)
-        pinned = [torch.from_numpy(a).pin_memory() for a in (P.reads, P.refs)]
-        keep.append(pinned)
-        pool.append(pf.Request(3, pinned[0].numpy(), pinned[1].numpy(), P.read_off, P.E))
+        pool.append(pf.Request(3, P.reads, P.refs, P.read_off, P.E, pinned=pinned))
+    return pool, sizes, rng
+
+
+def serve_reference_rates(pf, ctx, seed, n=4_000_000):
+    """The two numbers the offered loads are stated against: the batched
+    path's device throughput on a resident batch of the serving mix (pack +
+    filter with both deciders + compaction + verification, the same tuned
+    path the batched serving mode runs), and the host link's bound for the
+    serving mix (pinned host -> device copy rate / bytes moved per pair)."""
+    import torch
+    import synth
+    dev = torch.device("cuda", 0)
+    P = synth.generate(synth.SERVE, seed + 99, n, kmax=60)
+    reads_h = torch.from_numpy(P.reads).pin_memory()
+    reads = reads_h.to(dev)
+    refs = torch.from_numpy(P.refs).to(dev)
+    wo, total = pf.pf_pack_layout(P.read_off)
+    bo_d = torch.from_numpy(P.read_off).to(dev)
+    wo_d = torch.from_numpy(wo).to(dev)
+    rd = pf.Seqs.empty(total, dev, word_off=wo_d)
+    rf = pf.Seqs.empty(total, dev, word_off=wo_d)
+    pairs = pf.Pairs(rd, rf)
+    lens = torch.from_numpy(P.lens).to(dev)
+    E = torch.from_numpy(P.E).to(dev)
+    Emax = int(P.E.max())
+    acc = torch.empty(2 * n, dtype=torch.uint8, device=dev)
+    cnt = torch.empty(2 * n, dtype=torch.int16, device=dev)
+    dist = torch.empty(n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    pf.pf_pack(ctx, reads, bo_d, wo_d, rd)
+    pf.pf_pack(ctx, refs, bo_d, wo_d, rf)
+    pf.pf_tune_batch(ctx, 3, pairs, lens, E, Emax, n=n, sample=1 << 18, reps=1)
+
+    def step():
+        pf.pf_pack(ctx, reads, bo_d, wo_d, rd)
+        pf.pf_pack(ctx, refs, bo_d, wo_d, rf)
+        pf.pf_filter_verify(ctx, 3, pairs, lens, E, Emax, acc, cnt, dist, n)
+
+    for _ in range(3):
+        step()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(5):
+        step()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b) / 5
+    # host link: pinned -> device copies of the reads buffer
+    for _ in range(2):
+        reads.copy_(reads_h, non_blocking=True)
+    a.record(stream)
+    for _ in range(5):
+        reads.copy_(reads_h, non_blocking=True)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    h2d_gbs = 5 * reads_h.numel() / (a.elapsed_time(b) / 1000.0) / 1e9
+    bytes_per_pair = 2.0 * float(P.read_off[-1]) / n + 8 + 2   # ASCII, offset, threshold
+    return {"batched_peak_pairs_s": n / (ms / 1000.0), "batched_ms": ms, "batch_pairs": n,
+            "h2d_gbs": h2d_gbs, "h2d_bytes_per_pair": bytes_per_pair,
+            "link_bound_pairs_s": h2d_gbs * 1e9 / bytes_per_pair}
+
+
+def serve_measure(pf, ctx, seconds_per_load, seed, mode=0, ref=None, loads=(0.25, 0.5, 0.9)):
+    """Serving through pf_serve_replay.  Peak = pairs/s of a burst of every
+    request of the pool (four times over) submitted at once; then Poisson
+    arrivals at fractions of that peak and, when it is below the peak, at a
+    quarter of the batched path's device throughput (ref).  Latency = submit
+    to results in host memory."""
+    pool, sizes, rng = serve_pool(pf, seed)
     mean_pairs = float(sizes.mean())
-    pf.pf_serve_start(ctx)
+    pf.pf_serve_start(ctx, mode=mode)
     pf.pf_serve_replay(ctx, pool[:8], np.zeros(8))           # warm-up
     burst = np.zeros(4 * len(pool))
     st, lat, el = pf.pf_serve_replay(ctx, pool, burst)
     peak = 4 * float(sizes.sum()) / el
-    out = {"peak_pairs_s": peak, "requests_pool": len(pool), "mean_request_pairs": mean_pairs,
-           "status": int(st)}
-    for frac in (0.25, 0.5, 0.9):
-        lam = frac * peak / mean_pairs
+    out = {"mode": "batched" if mode == 0 else "device_loop", "peak_pairs_s": peak,
+           "requests_pool": len(pool), "mean_request_pairs": mean_pairs, "status": int(st),
+           "buffers": "page-locked host"}
+    points = [("load_%d" % int(f * 100), f * peak) for f in loads]
+    if ref and 0.25 * ref["batched_peak_pairs_s"] < 0.95 * peak:
+        points.append(("load_25_of_batched_peak", 0.25 * ref["batched_peak_pairs_s"]))
+    for name, offered in points:
+        lam = offered / mean_pairs
         count = max(50, int(lam * seconds_per_load))
         arr = np.cumsum(rng.exponential(1.0 / lam, size=count))
         st, lat, el = pf.pf_serve_replay(ctx, pool, arr)
         done_pairs = float(sum(sizes[i % len(pool)] for i in range(count)))
-        out["load_%d" % int(frac * 100)] = {
-            "offered_pairs_s": frac * peak, "throughput_pairs_s": done_pairs / el,
+        out[name] = {
+            "offered_pairs_s": offered, "throughput_pairs_s": done_pairs / el,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "requests": count, "status": int(st)}
     out["stats"] = pf.pf_serve_stats_get(ctx)
     pf.pf_serve_stop(ctx)
+    return out
+
+
+def serve_all(pf, seconds_per_load, seed, small_batch=1 << 16):
+    """Both serving modes on the same request pool, and the numbers the
+    offered loads are stated against.  A context of its own, tuned on a
+    resident batch of the serving mix (the batched mode copies its table)."""
+    ctx = pf.pf_create(0)
+    pf.pf_set_small_batch(ctx, small_batch)
+    ref = serve_reference_rates(pf, ctx, seed)
+    out = {"reference_rates": ref, "small_batch": small_batch}
+    out["batched"] = serve_measure(pf, ctx, seconds_per_load, seed, mode=0, ref=ref)
+    out["device_loop"] = serve_measure(pf, ctx, seconds_per_load / 2, seed, mode=1, ref=None)
+    pf.pf_destroy(ctx)
+    b = out["batched"]
+    out["note"] = ("offered loads are fractions of the measured serving peak; the batched "
+                   "path's device throughput on the serving mix is %.2fG pairs/s, but the "
+                   "requests' ASCII, offsets and thresholds (%.0f bytes per pair) cross a host "
+                   "link measured at %.0f GB/s, which bounds any served rate at %.2fG pairs/s "
+                   "(the serving peak reached %.0f%% of it), so loads of 50%% and 90%% of the "
+                   "batched peak cannot be offered"
+                   % (ref["batched_peak_pairs_s"] / 1e9, ref["h2d_bytes_per_pair"],
+                      ref["h2d_gbs"], ref["link_bound_pairs_s"] / 1e9,
+                      100.0 * b["peak_pairs_s"] / ref["link_bound_pairs_s"]))
     return out
 
 
@@ -305,14 +398,16 @@ def run_other_workload(args):
     if w == "cfg2_sweep":
         run_threshold_sweep(args, pf, ctx, timed, dev)
         return
+    size = args.other_pairs
     if w == "cfg1":   # plain SneakySnake, 100k pairs of 100 bp from ASCII, E = 5
-        P = synth.generate(synth.UNIFORM, 0x5EED0000, 100_000, m=100, E=5, kmax=20)
+        P = synth.generate(synth.UNIFORM, 0x5EED0000, size or 100_000, m=100, E=5, kmax=20)
         fixed, Emax, kind = 100, 5, "uniform"
     elif w == "cfg3":  # 50M pairs, 100/150/250 bp, E = round(r*len)
-        P = synth.generate(synth.MIXED, 0x5EED0003, 50_000_000, kmax=60)
+        P = synth.generate(synth.MIXED, 0x5EED0003, size or 50_000_000, kmax=60)
         fixed, Emax, kind = None, int(P.E.max()), "mixed"
     else:              # cfg4: 10M pairs of 250 bp, E = 25
-        P = synth.generate(synth.SKEWED_ALL, 0x5EED0004, 10_000_000, m=250, E=25, kmax=100)
+        P = synth.generate(synth.SKEWED_ALL, 0x5EED0004, size or 10_000_000, m=250, E=25,
+                           kmax=100)
         fixed, Emax, kind = 250, 25, "skewed_all"
     n = P.n
     reads_h = torch.from_numpy(P.reads).pin_memory()
@@ -347,10 +442,22 @@ def run_other_workload(args):
         step = lambda: (pack(), pf.pf_filter(ctx, 1, pairs, lens, E, 5, acc, cnt, n))
         out["step"] = "pack + batched SneakySnake"
     else:
-        # the autotuner on the batch as it is: each threshold timed on up to
-        # 1M of its own pairs
-        pf.pf_tune_batch(ctx, 3, pairs, lens, E, Emax, n=n, sample=1 << 20, reps=1)
+        if args.cfg is not None:  # one forced configuration (profiling)
+            tpp, dpt, ecap, xe, words = pf.pf_kernel_configs()[args.cfg]
+            for e in range(Emax + 1):  # every threshold it serves: one launch
+                if (xe == e) or (xe < 0 and e <= ecap):
+                    pf.pf_tune_set(ctx, 3, e, args.cfg, args.chunk)
+        else:
+            # the autotuner on the batch as it is: each threshold timed on up
+            # to 1M of its own pairs
+            pf.pf_tune_batch(ctx, 3, pairs, lens, E, Emax, n=n, sample=1 << 20, reps=1)
         out["tuned_cfg"] = {int(e): pf.pf_tune_get(ctx, 3, int(e)) for e in np.unique(P.E)}
+        if args.stage == "filter_batched":  # the filter alone (profiling)
+            out["filter_ms"] = timed(
+                lambda: pf.pf_filter(ctx, 3, pairs, lens, E, Emax, acc, cnt, n), reps)
+            print(json.dumps(out), flush=True)
+            pf.pf_destroy(ctx)
+            return
         out["filter_ms"] = timed(lambda: pf.pf_filter(ctx, 3, pairs, lens, E, Emax, acc, cnt, n), reps)
         out["filter_verify_ms"] = timed(
             lambda: pf.pf_filter_verify(ctx, 3, pairs, lens, E, Emax, acc, cnt, dist, n), reps)
@@ -465,7 +572,7 @@ def main_gpu(args):
             dist.barrier()
 
     if args.stage == "serve":
-        out = serve_measure(pf, ctx, args.serve_seconds, SEED + 5 + rank)
+        out = serve_all(pf, args.serve_seconds, SEED + 5 + rank, args.serve_small_batch)
         if rank == 0:
             print(json.dumps({"stage": "serve", "serve": out}), flush=True)
         pf.pf_destroy(ctx)
@@ -618,7 +725,8 @@ def main_gpu(args):
     e2e_ms = max_over_ranks((time.perf_counter() - t_e) * 1000.0 / e2e_steps, dist)
     pf.pf_sync(ctx)
 
-    serve = None if args.no_serve else serve_measure(pf, ctx, args.serve_seconds, SEED + 5 + rank)
+    serve = (None if args.no_serve else
+             serve_all(pf, args.serve_seconds, SEED + 5 + rank, args.serve_small_batch))
 
     pk, pk_kind = peaks()
     stages = {"pack": pack_ms, "filter": filt_ms, "compact": compact_ms, "verify": verify_ms}
@@ -728,6 +836,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--pairs", type=int, default=N_PAIRS)
+    ap.add_argument("--other-pairs", type=int, default=None,
+                    help="batch size of --workload cfg1/cfg3/cfg4 (default: the "
+                         "configuration's own)")
     ap.add_argument("--cpu-sample", type=int, default=8_000_000,
                     help="pairs of the oracle's timed sample for cpu_baseline (about 10 s)")
     ap.add_argument("--cpu-sample-1t", type=int, default=300_000,
@@ -750,6 +861,8 @@ def main():
                     choices=["headline", "cfg1", "cfg3", "cfg4", "cfg2_sweep"],
                     help="other configurations, each on its own line")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-small-batch", type=int, default=1 << 16,
+                    help="serving batches below this many pairs take the plain kernel")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -242,6 +242,25 @@ PF_API pf_status pf_tune(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs,
                          const int32_t *lens, int E, int64_t n, int reps,
                          int *best_cfg, int *best_chunk, float *best_ms);
 
+/* ---- measurement: the integer-pipe peak ------------------------------------ */
+
+/* Microbenchmark of the integer pipes the filter runs on (no counterpart in
+ * the thesis; it measures the roofline's denominator on the GPU at hand).
+ * Every thread of a full-occupancy grid runs many independent dependency
+ * chains of one instruction mix, `launches` launches back to back on the
+ * context stream, timed with CUDA events after one warm-up launch (each
+ * launch takes tens of milliseconds):
+ *   kind 0  32-bit LOP3 and funnel-shift (SHF) instructions in equal
+ *           numbers: the map's and GateKeeper's mix
+ *   kind 1  POPC, each feeding a LOP3
+ * *ops_per_s (host) receives the instructions of the mix executed per
+ * second over all threads (one instruction of one thread = one op),
+ * *ms_per_launch (host, may be NULL) the mean launch time.  Synchronises
+ * the context stream.  PF_EINVAL for kind outside 0..1, launches outside
+ * 1..1000 or a NULL ops_per_s. */
+PF_API pf_status pf_peak_int(pf_ctx *ctx, int kind, int launches, double *ops_per_s,
+                             double *ms_per_launch);
+
 /* ---- a5: compaction ------------------------------------------------------ */
 
 /* Indices p (ascending) with flags[p] != 0, p < n, into idx (device
@@ -364,35 +383,64 @@ PF_API pf_status pf_run_host(pf_ctx *ctx, unsigned deciders, const uint8_t *read
                              const int16_t *E, int E_max, uint8_t *accept, int16_t *count,
                              int32_t *dist, int64_t n, int64_t chunk_pairs);
 
-/* ---- a8: serving (continuous batching over a device-resident loop) ------ */
+/* ---- a8: serving (continuous batching) ------------------------------------ */
 
 /* The accelerator of Ch. 4 streams pairs through its filtering units and
- * returns each decision as soon as it is made.  Here a persistent device
- * loop takes work items (chunks of admitted requests) from a ring in
- * mapped host memory; a host scheduler thread admits requests as slots and
- * device memory free up, stages their bytes, publishes their items, and
- * copies results back when the loop marks a request complete.  Requests
- * that arrive while others run are admitted and their chunks interleave on
- * the device.  Every device wait is bounded: the loop exits after
- * idle_exit_us without work (the scheduler relaunches it on demand) or when
- * stopped. */
+ * returns each decision as soon as it is made.  Here a host scheduler
+ * thread admits requests as they arrive, by slots and device memory, and
+ * feeds them to the GPU while earlier ones run; results go back to each
+ * request's host buffers as soon as its last pair is done.  Two modes:
+ *
+ * PF_SERVE_BATCHED (the default): continuous batching into device batches.
+ *   Admitted requests are placed, in arrival order, into the open batch;
+ *   their bytes are uploaded by the copy engine at once (a request larger
+ *   than the room left is split, the rest going to the next batch).  A batch
+ *   is launched as soon as fewer than two batches are on the GPU, so
+ *   requests that arrive while one runs gather in the next and batches grow
+ *   with the load.  Each batch runs the tuned path of pf_filter_verify
+ *   (pack, the scheduler's binned and tuned filter kernels, compaction,
+ *   verification) on its pairs, with the serving context's tuning table;
+ *   an epilogue kernel writes each pair's results into its request's
+ *   buffers (directly when they are page-locked).  hbm_budget sizes the
+ *   batch buffers; a request of any size streams through them.
+ * PF_SERVE_DEVICE_LOOP: a persistent device loop takes work items (chunks
+ *   of admitted requests) from a ring in mapped host memory and packs,
+ *   filters (a generic runtime-threshold kernel, 8 lanes per pair) and
+ *   verifies each chunk inside one block.  No launch per batch; a request
+ *   must fit the budget whole.  Every device wait is bounded: the loop
+ *   exits after idle_exit_us without work (the scheduler relaunches it on
+ *   demand) or when stopped. */
+#define PF_SERVE_BATCHED 0
+#define PF_SERVE_DEVICE_LOOP 1
+
 typedef struct {
-    size_t hbm_budget;   /* device bytes that admitted requests may hold;
-                            0 = the context's hbm_budget, else a quarter of
-                            free device memory */
+    size_t hbm_budget;   /* device bytes for admitted requests (device loop)
+                            or batch buffers (batched); 0 = the context's
+                            hbm_budget, else a quarter of free device memory */
     int max_requests;    /* requests admitted at once, 1..4096 (0 = 256) */
-    int chunk_pairs;     /* pairs per work item, 32..1024 (0 = 1024) */
-    int workers;         /* blocks of the device loop (0 = 2 per SM) */
-    int idle_exit_us;    /* the device loop ends after this long without
-                            work, 50..10^6 (0 = 500) */
+    int chunk_pairs;     /* device loop: pairs per work item, 32..1024
+                            (0 = 1024) */
+    int workers;         /* device loop: blocks of the loop (0 = 2 per SM) */
+    int idle_exit_us;    /* device loop: the loop ends after this long
+                            without work, 50..10^6 (0 = 500) */
     int start_paused;    /* nonzero: admit and stage, but run nothing until
                             pf_serve_resume */
+    int mode;            /* PF_SERVE_BATCHED or PF_SERVE_DEVICE_LOOP */
+    int batch_pairs;     /* batched: most pairs in one device batch, 0 = up
+                            to 2^22 as the budget allows; >= 1 */
+    int overlap_pairs;   /* batched: while a batch runs, the next one is
+                            launched beside it only once it holds this many
+                            pairs (else it keeps growing until the GPU has
+                            no batch); 0 = 2^18 */
 } pf_serve_config;
 
 /* One request: n pairs in HOST memory.  Pair p is reads[byte_off[p] ..
  * byte_off[p+1]) against refs[byte_off[p] .. byte_off[p+1]).  All buffers
  * belong to the caller and must stay valid until pf_wait/pf_poll reports
- * the request done.  Outputs as in pf_filter_verify: accept and count
+ * the request done.  Page-locked buffers are fastest: their bytes are
+ * uploaded asynchronously and, in the batched mode, the GPU reads offsets
+ * and thresholds and writes results in place; pageable ones are copied
+ * through pinned staging memory.  Outputs as in pf_filter_verify: accept and count
  * [slots*n], dist [n] = min(ED, E+1) for pairs the first selected decider
  * accepts, E+1 for the others. */
 typedef struct {
@@ -409,21 +457,33 @@ typedef struct {
 
 typedef struct {
     uint64_t submitted, completed, failed, pairs_completed;
-    uint64_t loop_launches;    /* times the device loop was (re)started */
+    uint64_t loop_launches;    /* device loop: times it was (re)started;
+                                  batched: device batches launched */
     /* seconds summed over completed requests: waiting for admission,
      * uploading, on the device (published to complete), results back */
     double queue_s, stage_s, device_s, drain_s;
     /* the longest single request in each of those phases, seconds */
     double queue_max_s, stage_max_s, device_max_s, drain_max_s;
+    /* batched mode: pairs over all batches, the largest batch, GPU time of
+     * the batches (from the end of their uploads to their last kernel), and
+     * the scheduler thread's time placing requests and enqueuing batches */
+    uint64_t batch_pairs, batch_pairs_max;
+    double batch_gpu_s, place_host_s, launch_host_s;
 } pf_serve_stats;
 
 /* Start serving on ctx (PF_EBUSY if already serving).  Allocates the
- * request arena, the ring and the scheduler thread. */
+ * device buffers of the mode, pinned staging memory and the scheduler
+ * thread.  The batched mode copies ctx's tuning table (pf_tune,
+ * pf_tune_batch, pf_tune_set, pf_set_small_batch, pf_set_resolve_by_bounds
+ * made before this call) into a private context of the serving thread, so
+ * calls on ctx may run beside it. */
 PF_API pf_status pf_serve_start(pf_ctx *ctx, const pf_serve_config *cfg);
 
 /* Queue a request; *ticket identifies it.  Malformed requests (null
  * pointers, decreasing offsets, E outside [0, PF_MAX_E]) return PF_EINVAL,
- * requests that could never fit the budget PF_ENOMEM; neither is queued. */
+ * requests that could never fit the budget PF_ENOMEM (device loop: the
+ * request whole; batched: one pair, or the pinned staging a pageable
+ * request needs); neither is queued. */
 PF_API pf_status pf_submit(pf_ctx *ctx, const pf_request *req, uint64_t *ticket);
 
 /* *done = 1 once the request's results are in its host buffers. */

@@ -74,6 +74,8 @@ def _load():
         lib.or_int_batch.restype = None
         lib.or_pack_batch.argtypes = [p, p, i64, p, p, p, p]
         lib.or_pack_batch.restype = i64
+        lib.or_work_counts.argtypes = [ctypes.c_char_p, ctypes.c_char_p, i32, i32, p]
+        lib.or_work_counts.restype = None
         _lib = lib
     return _lib
 
@@ -218,7 +220,7 @@ def filter_batch(pairs, deciders=SNEAKYSNAKE | GATEKEEPER, E=None, threads=None)
 
 
 _KINDS = {"wf_banded": 1, "wf": 2, "ss_dp": 3, "ss_full": 4, "hamming": 5,
-          "ss_partitioned": 6, "shouji": 7, "gk_shd": 8}
+          "ss_partitioned": 6, "shouji": 7, "gk_shd": 8, "work": 9}
 
 
 def int_batch(kind, pairs, E=None, threads=None, p0=0, p1=0):
@@ -233,6 +235,27 @@ def int_batch(kind, pairs, E=None, threads=None, p0=0, p1=0):
                      _ptr(pairs.ref_off), _ptr(np.ascontiguousarray(pairs.lens, np.int32)),
                      _ptr(e), stride, _ptr(out), n, _threads(threads), int(p0), int(p1))
     return out
+
+
+def work_counts(R, F, E):
+    """(SneakySnake search words, SneakySnake columns, GateKeeper Hamming
+    columns, GateKeeper AND columns) the method needs for one pair."""
+    R, F = _b(R), _b(F)
+    out = np.zeros(4, dtype=np.int32)
+    _load().or_work_counts(R, F, len(R), E, _ptr(out))
+    return tuple(int(x) for x in out)
+
+
+def work_batch(pairs, E=None, threads=None):
+    """work_counts for every pair of a batch: int32[n, 4]."""
+    lib = _load()
+    n = pairs.n
+    e, stride = _E_arr(pairs.E if E is None else E)
+    out = np.zeros((max(n, 1), 4), dtype=np.int32)
+    lib.or_int_batch(9, _ptr(pairs.reads), _ptr(pairs.read_off), _ptr(pairs.refs),
+                     _ptr(pairs.ref_off), _ptr(np.ascontiguousarray(pairs.lens, np.int32)),
+                     _ptr(e), stride, _ptr(out), n, _threads(threads), 0, 0)
+    return out[:n]
 
 
 def verify_batch(pairs, E=None, threads=None):

@@ -332,6 +332,84 @@ int or_gatekeeper(const uint8_t *R, const uint8_t *F, int m, int E)
 }
 
 /* ------------------------------------------------------------------ */
+/* Work the method needs per pair (a measurement aid, not a result)    */
+/* ------------------------------------------------------------------ */
+
+/* How much of the map each decider needs before its answer is known, for
+ * the "needed work" roofline of a word-parallel implementation that stops
+ * a pair once both deciders are decided.  Changes no result.
+ *   out[0]  SneakySnake: 32-column words spanned by its deepest-pipe
+ *           searches, summed over the searches the walk of §8.4.2 makes
+ *           with the limit of R5 (a search from column c whose deepest
+ *           pipe ends at column e (its obstacle, or the last column) spans
+ *           the words of columns c..e);
+ *   out[1]  SneakySnake: leading columns it reads (through the last
+ *           obstacle it meets, or all m);
+ *   out[2]  GateKeeper: leading columns the Hamming count of §5.2.1 needs
+ *           (all m when it is at most E; else through the column where it
+ *           first exceeds E);
+ *   out[3]  GateKeeper: leading columns the amended-mask AND of §5.2.2-
+ *           §5.2.3 needs (0 when the Hamming check accepts; through the
+ *           column where the AND's popcount first exceeds E, plus the two
+ *           columns an amended bit looks ahead, when it rejects; else m). */
+void or_work_counts(const uint8_t *R, const uint8_t *F, int m, int E, int *out)
+{
+    out[0] = out[1] = out[2] = out[3] = 0;
+    if (m <= 0) return;
+    uint8_t *map = (uint8_t *)malloc((size_t)(2 * E + 1) * m);
+    or_neighborhood_map(R, F, m, E, map);
+    /* the walk of or_snake_walk, counting what it reads */
+    int c = 0, k = 0, words = 0, cols = 0;
+    for (;;) {
+        int best = 0;
+        for (int d = -E; d <= E; ++d) {
+            int r = or_pipe_depth(map, m, E, d, c);
+            if (r > best) best = r;
+        }
+        int end = c + best < m ? c + best : m - 1;   /* last column this search reads */
+        words += end / 32 - c / 32 + 1;
+        if (end + 1 > cols) cols = end + 1;
+        c += best;
+        if (c >= m) break;
+        k += 1;
+        c += 1;
+        if (c >= m) break;
+        if (k > E) break;
+    }
+    out[0] = words;
+    out[1] = cols;
+    /* GateKeeper's prefix counts */
+    int h = or_hamming(R, F, m);
+    if (h <= E) {
+        out[2] = m;
+        out[3] = 0;
+    } else {
+        int run = 0, i = 0;
+        for (; i < m; ++i) {
+            run += or_match(R[i], F[i]) ? 0 : 1;
+            if (run > E) break;
+        }
+        out[2] = i + 1;
+        uint8_t *amended = (uint8_t *)malloc((size_t)m);
+        uint8_t *fin = (uint8_t *)malloc((size_t)m);
+        for (int x = 0; x < m; ++x) fin[x] = 1;
+        for (int d = -E; d <= E; ++d) {
+            or_amend(map + (size_t)(d + E) * m, m, amended);
+            for (int x = 0; x < m; ++x) fin[x] = fin[x] & amended[x];
+        }
+        int cnt = 0, x = 0;
+        for (; x < m; ++x) {
+            cnt += fin[x];
+            if (cnt > E) break;
+        }
+        out[3] = (x < m) ? (x + 3 < m ? x + 3 : m) : m;
+        free(fin);
+        free(amended);
+    }
+    free(map);
+}
+
+/* ------------------------------------------------------------------ */
 /* SneakySnake on sub-matrices of t columns (§8.5, R15)                */
 /* ------------------------------------------------------------------ */
 
@@ -543,7 +621,8 @@ typedef struct {
     int64_t n, begin, end;
     int kind; /* 0 filter, 1 verify, 2 full WF, 3 SS dp, 4 SS full, 5 hamming,
                  6 partitioned SS (p0 = t, p1 = y), 7 Shouji,
-                 8 SHD-style GateKeeper (p0 = vacant zero, p1 = streak) */
+                 8 SHD-style GateKeeper (p0 = vacant zero, p1 = streak),
+                 9 work counts (four ints per pair) */
     int p0, p1;
 } or_job;
 
@@ -579,6 +658,7 @@ static void *or_run_job(void *arg)
         case 6: j->dist[p] = or_sneakysnake_partitioned(R, F, m, E, j->p0, j->p1); break;
         case 7: j->dist[p] = or_shouji(R, F, m, E); break;
         case 8: j->dist[p] = or_gatekeeper_shd(R, F, m, E, j->p0, j->p1); break;
+        case 9: or_work_counts(R, F, m, E, j->dist + 4 * p); break;
         }
     }
     return NULL;
@@ -624,7 +704,8 @@ void or_filter_batch(const uint8_t *reads, const int64_t *read_off,
 /* Per-pair integer results: kind 1 banded WF min(ED, E+1), 2 full WF,
  * 3 SneakySnake DP formulation, 4 unsaturated SneakySnake, 5 Hamming,
  * 6 partitioned SneakySnake (p0 = t, p1 = y), 7 Shouji, 8 SHD-style
- * GateKeeper (p0 = vacant zero, p1 = streak counting). */
+ * GateKeeper (p0 = vacant zero, p1 = streak counting), 9 the work counts
+ * of or_work_counts (out holds 4 n ints). */
 void or_int_batch(int kind, const uint8_t *reads, const int64_t *read_off,
                   const uint8_t *refs, const int64_t *ref_off,
                   const int32_t *lens, const int16_t *E, int E_stride,

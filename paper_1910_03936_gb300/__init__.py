@@ -24,7 +24,7 @@ __all__ = [
     "pf_serve_resume", "pf_serve_stats_get", "pf_serve_stop", "pf_serve_replay", "pf_run_host",
     "pf_filter_partitioned", "pf_filter_shouji", "pf_filter_shd", "PF_SHD_VACANT_ZERO",
     "PF_SHD_STREAK", "pf_set_small_batch", "pf_tune_batch", "pf_set_resolve_by_bounds",
-    "pf_last_verified_count",
+    "pf_last_verified_count", "pf_peak_int", "PF_SERVE_BATCHED", "PF_SERVE_DEVICE_LOOP",
 ]
 
 PF_SNEAKYSNAKE = 1
@@ -32,6 +32,8 @@ PF_GATEKEEPER = 2
 PF_MAX_E = 31
 PF_SHD_VACANT_ZERO = 1
 PF_SHD_STREAK = 2
+PF_SERVE_BATCHED = 0
+PF_SERVE_DEVICE_LOOP = 1
 
 _STATUS = {0: "PF_OK", 1: "PF_EINVAL", 2: "PF_ENOMEM", 3: "PF_ECUDA", 4: "PF_ETIMEOUT",
            5: "PF_EBUSY", 6: "PF_ECANCELLED", 7: "PF_EDATA"}
@@ -60,7 +62,9 @@ class _Pairs(ctypes.Structure):
 class ServeConfig(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_size_t), ("max_requests", ctypes.c_int),
                 ("chunk_pairs", ctypes.c_int), ("workers", ctypes.c_int),
-                ("idle_exit_us", ctypes.c_int), ("start_paused", ctypes.c_int)]
+                ("idle_exit_us", ctypes.c_int), ("start_paused", ctypes.c_int),
+                ("mode", ctypes.c_int), ("batch_pairs", ctypes.c_int),
+                ("overlap_pairs", ctypes.c_int)]
 
 
 class _Request(ctypes.Structure):
@@ -78,7 +82,9 @@ class ServeStats(ctypes.Structure):
                 ("stage_s", ctypes.c_double), ("device_s", ctypes.c_double),
                 ("drain_s", ctypes.c_double), ("queue_max_s", ctypes.c_double),
                 ("stage_max_s", ctypes.c_double), ("device_max_s", ctypes.c_double),
-                ("drain_max_s", ctypes.c_double)]
+                ("drain_max_s", ctypes.c_double), ("batch_pairs", ctypes.c_uint64),
+                ("batch_pairs_max", ctypes.c_uint64), ("batch_gpu_s", ctypes.c_double),
+                ("place_host_s", ctypes.c_double), ("launch_host_s", ctypes.c_double)]
 
 
 _lib = None
@@ -130,6 +136,8 @@ def load():
         "pf_set_small_batch": [P, I64],
         "pf_set_resolve_by_bounds": [P, I],
         "pf_last_verified_count": [P, ctypes.POINTER(ctypes.c_int64)],
+        "pf_peak_int": [P, I, I, ctypes.POINTER(ctypes.c_double),
+                        ctypes.POINTER(ctypes.c_double)],
         "pf_tune_batch": [P, U, ctypes.POINTER(_Pairs), P, P, I, I64, I64, I],
         "pf_tune_get": [P, U, I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
         "pf_tune": [P, U, ctypes.POINTER(_Pairs), P, I, I64, I, ctypes.POINTER(ctypes.c_int),
@@ -466,6 +474,16 @@ def pf_last_verified_count(ctx):
     return v.value
 
 
+def pf_peak_int(ctx, kind=0, launches=30):
+    """Integer-pipe microbenchmark: (instructions/s, ms per launch) of the
+    LOP3+SHF mix (kind 0) or POPC+LOP3 (kind 1) over a full-occupancy grid."""
+    ops, ms = ctypes.c_double(), ctypes.c_double()
+    _cur_stream(ctx)
+    _check(load().pf_peak_int(ctx.handle, int(kind), int(launches), ctypes.byref(ops),
+                              ctypes.byref(ms)), ctx.handle)
+    return ops.value, ms.value
+
+
 def pf_tune_get(ctx, deciders, E):
     c, k = ctypes.c_int(), ctypes.c_int()
     _check(load().pf_tune_get(ctx.handle, int(deciders), int(E), ctypes.byref(c), ctypes.byref(k)),
@@ -489,28 +507,48 @@ def pf_tune(ctx, deciders, pairs, lens, E, n=None, reps=3):
 # ---- a8 serving -----------------------------------------------------------
 
 def pf_serve_start(ctx, hbm_budget=0, max_requests=0, chunk_pairs=0, workers=0,
-                   idle_exit_us=0, start_paused=False):
+                   idle_exit_us=0, start_paused=False, mode=0, batch_pairs=0, overlap_pairs=0):
+    """Start serving; mode PF_SERVE_BATCHED (0) or PF_SERVE_DEVICE_LOOP (1)."""
     cfg = ServeConfig(hbm_budget, max_requests, chunk_pairs, workers, idle_exit_us,
-                      1 if start_paused else 0)
+                      1 if start_paused else 0, int(mode), int(batch_pairs), int(overlap_pairs))
     _check(load().pf_serve_start(ctx.handle, ctypes.byref(cfg)), ctx.handle)
 
 
 class Request:
     """A request in host memory (numpy arrays).  The arrays are kept
-    referenced here until the request is waited for."""
+    referenced here until the request is waited for.  pinned=True copies the
+    inputs into, and allocates the outputs in, page-locked memory (the fast
+    path: asynchronous uploads, results written in place by the GPU)."""
 
-    def __init__(self, deciders, reads, refs, byte_off, E):
+    def __init__(self, deciders, reads, refs, byte_off, E, pinned=False):
         import numpy as np
-        self.reads = np.ascontiguousarray(reads, dtype=np.uint8)
-        self.refs = np.ascontiguousarray(refs, dtype=np.uint8)
-        self.byte_off = np.ascontiguousarray(byte_off, dtype=np.int64)
-        self.E = np.ascontiguousarray(E, dtype=np.int16)
+
+        def host(a, dtype):
+            a = np.ascontiguousarray(a, dtype=dtype)
+            if pinned:
+                t = torch.from_numpy(a.copy() if a.size else np.zeros(1, dtype)).pin_memory()
+                self._keep.append(t)
+                return t.numpy()[:a.size]
+            return a
+
+        def zeros(count, dtype):
+            if pinned:
+                t = torch.zeros(count, dtype=dtype).pin_memory()
+                self._keep.append(t)
+                return t.numpy()
+            return np.zeros(count, dtype=torch.empty(0, dtype=dtype).numpy().dtype)
+
+        self._keep = []
+        self.reads = host(reads, np.uint8)
+        self.refs = host(refs, np.uint8)
+        self.byte_off = host(byte_off, np.int64)
+        self.E = host(E, np.int16)
         self.n = len(self.byte_off) - 1
         slots = 2 if deciders == 3 else 1
         self.deciders = deciders
-        self.accept = np.zeros(slots * max(self.n, 1), dtype=np.uint8)
-        self.count = np.zeros(slots * max(self.n, 1), dtype=np.int16)
-        self.dist = np.zeros(max(self.n, 1), dtype=np.int32)
+        self.accept = zeros(slots * max(self.n, 1), torch.uint8)
+        self.count = zeros(slots * max(self.n, 1), torch.int16)
+        self.dist = zeros(max(self.n, 1), torch.int32)
         self.ticket = None
 
     def _c(self):

@@ -309,10 +309,14 @@ pf_status pf_ctx::run_batched(unsigned dec, const FilterArgs &a, const Scratch &
     if (used.size() == 1) {
         const int c = used[0];
         b.chunk = tune_chunk[dec][a.E_max];
-        const int64_t items = (a.n + b.chunk - 1) / b.chunk;
+        // enough warps for each to take one step of pairs at once (the
+        // kernels shrink their work items to spread a short batch over the
+        // grid), at most one resident wave
+        const int64_t steps = (a.n + cfg_step(kBatchCfgs[c], (int)dec) - 1) /
+                              cfg_step(kBatchCfgs[c], (int)dec);
         const int wpb = cfg_threads(kBatchCfgs[c], (int)dec) / 32;  // warps per block
         const int grid = (int)std::min<int64_t>(grid_for(dec, c),
-                                                std::max<int64_t>(1, (items + wpb - 1) / wpb));
+                                                std::max<int64_t>(1, (steps + wpb - 1) / wpb));
         return cuda(launch_filter_batched(dec, c, grid, b, c, stream), "filter launch");
     }
     // several configurations: one persistent launch each, concurrently
@@ -698,9 +702,10 @@ pf_status pf_tune_batch(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs,
             for (int k : chunks) {
                 b.chunk = k;
                 const int wpb = cfg_threads(kBatchCfgs[c], (int)deciders) / 32;
-                const int64_t items = (hi - lo + k - 1) / k;
+                const int step = cfg_step(kBatchCfgs[c], (int)deciders);
+                const int64_t steps = (hi - lo + step - 1) / step;
                 const int grid = (int)std::min<int64_t>(ctx->grid_for((int)deciders, c),
-                                                        std::max<int64_t>(1, (items + wpb - 1) / wpb));
+                                                        std::max<int64_t>(1, (steps + wpb - 1) / wpb));
                 float best = 1e30f;
                 for (int rep = 0; rep <= reps && st == PF_OK; ++rep) {  // the first run warms up
                     cudaMemsetAsync(b.work, 0, sizeof(unsigned long long), ctx->stream);

@@ -161,15 +161,15 @@ struct PairFilter {
     __device__ __forceinline__ void run(const PairsView &pv, int g, unsigned gmask) {
         if constexpr (!GK) {  // no history to rotate
             while (!done()) word(pv, g, gmask, P0, P2, P1);
-            return;
-        }
-        for (;;) {
-            if (done()) { role = 0; return; }
-            word(pv, g, gmask, P0, P2, P1);
-            if (done()) { role = 1; return; }
-            word(pv, g, gmask, P1, P0, P2);
-            if (done()) { role = 2; return; }
-            word(pv, g, gmask, P2, P1, P0);
+        } else {
+            for (;;) {
+                if (done()) { role = 0; return; }
+                word(pv, g, gmask, P0, P2, P1);
+                if (done()) { role = 1; return; }
+                word(pv, g, gmask, P1, P0, P2);
+                if (done()) { role = 2; return; }
+                word(pv, g, gmask, P2, P1, P0);
+            }
         }
     }
 
@@ -456,8 +456,24 @@ __global__ void __launch_bounds__(256) filter_plain_kernel(FilterArgs a) {
     filter_group<1, DPT, DEC>(a, p, 0, 1u << (threadIdx.x & 31));
 }
 
+// Pairs per work item of a persistent launch over a bin of `bin_pairs`
+// pairs: the tuned chunk, unless the bin is too short to give every warp of
+// the grid one item of that size.  Then the items shrink (to a multiple of
+// the pairs a warp takes at once, `step`) so that the bin spreads over the
+// whole grid: a pair's latency is long (up to thousands of dependent
+// instructions), and a short bin left to a few warps, each running a chain
+// of pairs, would finish long after the rest of the GPU went idle.  Every
+// warp computes the same value.
+__device__ __forceinline__ int64_t item_pairs(int64_t bin_pairs, int tuned, int step) {
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    int64_t c = (bin_pairs + warps - 1) / warps;
+    c = (c + step - 1) / step * step;
+    if (c < step) c = step;
+    return c < tuned ? c : (int64_t)tuned;
+}
+
 // The batched kernel: persistent warps take chunks of `chunk` positions of
-// one bin through an atomic counter; the lane groups of a warp stride
+// one bin through an atomic counter (fewer for a short bin, item_pairs); the lane groups of a warp stride
 // through the chunk, one pair per group at a time, so neighbouring groups
 // read neighbouring pairs' words.
 template <int TPP, int DPT, int DEC, int XE>
@@ -469,15 +485,16 @@ __global__ void __launch_bounds__(256) filter_batched_kernel(BatchArgs b, int bi
     constexpr int GPW = 32 / TPP;  // groups per warp
     const int gid = lane / TPP;
     const int64_t lo = b.bin_start[bin], hi = b.bin_start[bin + 1];
+    const int64_t chunk = item_pairs(hi - lo, b.chunk, GPW);
     unsigned long long *counter = b.work + bin;
     const int64_t *order = (b.order && !(b.ident && *b.ident)) ? b.order : nullptr;
     for (;;) {
         unsigned long long item = 0;
         if (lane == 0) item = atomicAdd(counter, 1ull);
         item = __shfl_sync(0xffffffffu, item, 0);
-        const int64_t s = lo + (int64_t)item * b.chunk;
+        const int64_t s = lo + (int64_t)item * chunk;
         if (s >= hi) break;
-        const int64_t e = min(hi, s + (int64_t)b.chunk);
+        const int64_t e = min(hi, s + chunk);
         for (int64_t q = s + gid; q < e; q += GPW) {
             const int64_t p = order ? __ldg(order + q) : q;
             filter_group<TPP, DPT, DEC, XE>(b.f, p, g, gmask);
@@ -570,15 +587,16 @@ __global__ void __launch_bounds__(kSplitWarps * 32, (XE <= 7 ? 5 : (XE <= 10 ? 4
     const int lane = threadIdx.x & 31;
     uint32_t *mine = split_maps + (threadIdx.x >> 5) * (WMAX * NS * 32) + lane;
     const int64_t lo = b.bin_start[bin], hi = b.bin_start[bin + 1];
+    const int64_t chunk = item_pairs(hi - lo, b.chunk, 32);
     unsigned long long *counter = b.work + bin;
     const int64_t *order = (b.order && !(b.ident && *b.ident)) ? b.order : nullptr;
     for (;;) {
         unsigned long long item = 0;
         if (lane == 0) item = atomicAdd(counter, 1ull);
         item = __shfl_sync(0xffffffffu, item, 0);
-        const int64_t s = lo + (int64_t)item * b.chunk;
+        const int64_t s = lo + (int64_t)item * chunk;
         if (s >= hi) break;
-        const int64_t e = min(hi, s + (int64_t)b.chunk);
+        const int64_t e = min(hi, s + chunk);
         for (int64_t q = s + lane; q < e; q += 32) {
             const int64_t p = order ? __ldg(order + q) : q;
             filter_split_pair<DEC, XE, WMAX>(b.f, p, mine, 1u << lane);

@@ -55,6 +55,12 @@ constexpr size_t cfg_smem(const KernelCfg &c, int dec) {
                : 0;
 }
 
+// Pairs one warp of a configuration's kernel takes at once: one per lane in
+// the two-phase form, one per lane group in the fused loop.
+constexpr int cfg_step(const KernelCfg &c, int dec) {
+    return cfg_split(c, dec) ? 32 : 32 / c.tpp;
+}
+
 // a configuration serves threshold E
 constexpr bool cfg_serves(const KernelCfg &c, int E) {
     return c.xe >= 0 ? c.xe == E : c.ecap >= E;
@@ -74,7 +80,8 @@ const void *filter_batched_fn(int dec, int cfg);
 
 cudaError_t launch_pack_ragged(const uint8_t *ascii, const int64_t *byte_off,
                                const int64_t *word_off, int64_t nseq, uint32_t *lo,
-                               uint32_t *hi, uint32_t *nm, unsigned *err, cudaStream_t st);
+                               uint32_t *hi, uint32_t *nm, unsigned *err, cudaStream_t st,
+                               const int32_t *seg_of = nullptr, unsigned *seg_err = nullptr);
 cudaError_t launch_pack_fixed(const uint8_t *ascii, int64_t nseq, int len, uint32_t *lo,
                               uint32_t *hi, uint32_t *nm, unsigned *err, int sms,
                               cudaStream_t st);

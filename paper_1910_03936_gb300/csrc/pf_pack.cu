@@ -75,19 +75,24 @@ __device__ __forceinline__ void decode_chunks(uintptr_t cbase, int nchunks, uint
 // the fixed layout does, was slower here: the extra round of memory latency
 // for the offsets and the binary search per word left too little work per
 // block to hide it.)  Words past ceil(len/32) of a sequence (a word_off
-// with room to spare) are all N.
+// with room to spare) are all N.  With seg_of given, a byte error of
+// sequence s is recorded in seg_err[seg_of[s]] instead of err (the serving
+// batches attribute errors to the request a sequence came from).
 constexpr int kSeqPerBlock = 128;
 
 __global__ void __launch_bounds__(kPackThreads, 8)
 pack_ragged_kernel(const uint8_t *ascii, const int64_t *byte_off, const int64_t *word_off,
-                   int64_t nseq, uint32_t *lo, uint32_t *hi, uint32_t *nm, unsigned *err) {
+                   int64_t nseq, uint32_t *lo, uint32_t *hi, uint32_t *nm, unsigned *err,
+                   const int32_t *seg_of, unsigned *seg_err) {
     __shared__ int64_t woff[kSeqPerBlock + 1];
     __shared__ int64_t boff[kSeqPerBlock + 1];
+    __shared__ int32_t sseg[kSeqPerBlock];
     const int64_t s0 = (int64_t)blockIdx.x * kSeqPerBlock;
     const int ns = (int)min((int64_t)kSeqPerBlock, nseq - s0);
     for (int i = threadIdx.x; i <= ns; i += blockDim.x) {
         woff[i] = word_off[s0 + i];
         boff[i] = byte_off[s0 + i];
+        if (seg_of && i < ns) sseg[i] = seg_of[s0 + i];
     }
     __syncthreads();
     const uint8_t *lim = ascii + __ldg(byte_off + nseq);
@@ -108,7 +113,8 @@ pack_ragged_kernel(const uint8_t *ascii, const int64_t *byte_off, const int64_t 
             nm[gw] = 0xffffffffu;
             continue;
         }
-        pack_word(ascii + boff[l], len, w, lo + gw, hi + gw, nm + gw, err, lim);
+        pack_word(ascii + boff[l], len, w, lo + gw, hi + gw, nm + gw,
+                  seg_of ? seg_err + sseg[l] : err, lim);
     }
 }
 
@@ -226,11 +232,12 @@ pack_stream_kernel(const uint8_t *ascii, int64_t nseq, int len, int W, uint32_t 
 
 cudaError_t launch_pack_ragged(const uint8_t *ascii, const int64_t *byte_off,
                                const int64_t *word_off, int64_t nseq, uint32_t *lo,
-                               uint32_t *hi, uint32_t *nm, unsigned *err, cudaStream_t st) {
+                               uint32_t *hi, uint32_t *nm, unsigned *err, cudaStream_t st,
+                               const int32_t *seg_of, unsigned *seg_err) {
     if (nseq <= 0) return cudaSuccess;
     const int64_t blocks = (nseq + kSeqPerBlock - 1) / kSeqPerBlock;
-    pack_ragged_kernel<<<(unsigned)blocks, kPackThreads, 0, st>>>(ascii, byte_off, word_off,
-                                                                 nseq, lo, hi, nm, err);
+    pack_ragged_kernel<<<(unsigned)blocks, kPackThreads, 0, st>>>(
+        ascii, byte_off, word_off, nseq, lo, hi, nm, err, seg_of, seg_err);
     return cudaGetLastError();
 }
 

@@ -21,7 +21,11 @@
 #include <thread>
 #include <vector>
 
-#include "pf_ctx.h"
+#if defined(__linux__)
+#include <sys/prctl.h>
+#endif
+
+#include "pf_serve.h"
 #include "pf_filter.cuh"
 #include "pf_pack.cuh"
 #include "pf_verify.cuh"
@@ -34,37 +38,6 @@ constexpr int kServeTpp = 8;      // lanes per pair in the loop's filter
 constexpr int kServeDpt = 8;      // slots per lane: E <= 31
 constexpr uint64_t kRingSize = 1u << 16;
 
-// Per-slot request descriptor, in device memory (uploaded with the request).
-struct ServeDesc {
-    const uint8_t *reads, *refs;
-    const int64_t *byte_off;   // the caller's offsets (not rebased)
-    int64_t *word_off;         // filled by the loop, chunk by chunk
-    const int16_t *E;
-    uint32_t *rlo, *rhi, *rnm, *flo, *fhi, *fnm;
-    uint8_t *accept;
-    int16_t *count;
-    int32_t *dist;
-    unsigned *err;
-    int64_t n;
-    int chunk, nchunks;
-    unsigned deciders;
-    unsigned epoch;
-};
-
-struct ServeDevice {
-    const ServeDesc *desc;            // [max_requests], device
-    unsigned *done;                   // [max_requests], device: chunks finished
-    unsigned long long *head;         // device: next item to claim
-    const unsigned long long *items;  // mapped host ring
-    const unsigned long long *tail;   // mapped host: items published
-    const unsigned *stop;             // mapped host
-    unsigned *complete;               // mapped host [max_requests]: epoch of the finished request
-    unsigned long long *last_claim;   // device: globaltimer of the latest claim, any block
-    unsigned long long *dev_tail;     // device: mirror of *tail
-    unsigned long long *last_poll;    // device: globaltimer of the latest mirror refresh
-    unsigned *dev_exit;               // device: set by a block that finds the loop idle or stopped
-    unsigned long long idle_ns;
-};
 
 __device__ __forceinline__ unsigned long long ld_acquire_sys(const unsigned long long *p) {
     unsigned long long v;
@@ -293,108 +266,8 @@ __global__ void __launch_bounds__(kServeThreads) serve_loop_kernel(ServeDevice s
 // ---------------------------------------------------------------------------
 // host side
 
-struct ServeReq {
-    uint64_t ticket = 0;
-    pf_request req{};
-    int slot = -1;
-    size_t off = 0, bytes = 0;     // device arena
-    size_t hoff = 0, hbytes = 0;   // pinned staging arena
-    int64_t total_bytes = 0, total_words = 0;
-    int nchunks = 0;
-    unsigned epoch = 0;
-    bool pinned_in = false;        // reads and refs are page-locked
-    enum State { PENDING, STAGING, RUNNING, DRAINING, DONE } state = PENDING;
-    cudaEvent_t ev = nullptr;
-    using tp = std::chrono::steady_clock::time_point;
-    tp t_submit, t_admit, t_pub, t_seen, t_done;
-    pf_status status = PF_OK;
-    // pinned staging pieces
-    int64_t *h_boff = nullptr;
-    int16_t *h_E = nullptr;
-    uint8_t *h_acc = nullptr;
-    int16_t *h_cnt = nullptr;
-    int32_t *h_dist = nullptr;
-    unsigned *h_err = nullptr;
-};
-
-// First-fit allocator over [0, size) for the two arenas.
-struct Arena {
-    std::map<size_t, size_t> free_list;  // offset -> size
-    void reset(size_t size) {
-        free_list.clear();
-        if (size) free_list[0] = size;
-    }
-    bool alloc(size_t bytes, size_t *off) {
-        for (auto it = free_list.begin(); it != free_list.end(); ++it) {
-            if (it->second >= bytes) {
-                *off = it->first;
-                const size_t rest = it->second - bytes;
-                const size_t o = it->first + bytes;
-                free_list.erase(it);
-                if (rest) free_list[o] = rest;
-                return true;
-            }
-        }
-        return false;
-    }
-    void release(size_t off, size_t bytes) {
-        auto it = free_list.emplace(off, bytes).first;
-        auto nx = std::next(it);
-        if (nx != free_list.end() && it->first + it->second == nx->first) {
-            it->second += nx->second;
-            free_list.erase(nx);
-        }
-        if (it != free_list.begin()) {
-            auto pv = std::prev(it);
-            if (pv->first + pv->second == it->first) {
-                pv->second += it->second;
-                free_list.erase(it);
-            }
-        }
-    }
-};
-
-struct ServeState {
-    pf_serve_config cfg{};
-    int device = 0;
-    size_t budget = 0, stage_budget = 0;
-    char *arena = nullptr;         // device
-    char *stage_mem = nullptr;     // pinned host
-    Arena dev_arena, host_arena;
-    ServeDesc *d_desc = nullptr;
-    ServeDesc *h_desc = nullptr;   // pinned staging, one per slot
-    unsigned *d_done = nullptr;
-    unsigned long long *d_head = nullptr, *d_last = nullptr, *d_tail = nullptr, *d_poll = nullptr;
-    unsigned *d_exit = nullptr;
-    unsigned long long *h_items = nullptr, *h_tail = nullptr;
-    unsigned *h_stop = nullptr, *h_complete = nullptr;
-    ServeDevice dev{};
-    cudaStream_t s_copy = nullptr, s_loop = nullptr;
-    cudaEvent_t ev_loop = nullptr;
-    bool loop_running = false;
-    std::atomic<bool> paused{false};
-    uint64_t published = 0;        // items published (host copy of *h_tail)
-    uint64_t inflight_items = 0;
-
-    std::mutex mu;
-    std::condition_variable cv_work, cv_done, cv_idle;
-    bool quit = false;
-    int waiters = 0;               // threads inside pf_wait
-    std::thread th;
-    uint64_t next_ticket = 1;
-    std::deque<std::shared_ptr<ServeReq>> pending;
-    std::vector<std::shared_ptr<ServeReq>> active;      // admitted, not done
-    std::map<uint64_t, std::shared_ptr<ServeReq>> reqs; // every unreleased ticket
-    std::vector<int> free_slots;
-    std::vector<unsigned> slot_epoch;
-    pf_serve_stats stats{};
-    std::string fatal;
-};
-
 namespace {
 
-inline size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
-inline int slots_of(unsigned deciders) { return deciders == 3u ? 2 : 1; }
 
 // Device bytes a request needs in the arena.
 size_t request_bytes(const pf_request &r, int64_t total_bytes, int64_t total_words) {
@@ -409,19 +282,6 @@ size_t staging_bytes(const pf_request &r) {
     const size_t n = (size_t)r.n, sl = (size_t)slots_of(r.deciders);
     return up256((n + 1) * 8) + up256(n * 2) + up256(sl * n) + up256(sl * n * 2) +
            up256(n * 4) + 256;
-}
-
-bool is_pinned(const void *p) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeHost;
-}
-
-double secs(ServeReq::tp a, ServeReq::tp b) {
-    return std::chrono::duration<double>(b - a).count();
 }
 
 void stage(ServeState &S, ServeReq &q) {
@@ -531,6 +391,9 @@ void finish_req(ServeState &S, ServeReq &q, pf_status st, bool copy_out) {
 void scheduler(ServeState *Sp) {
     ServeState &S = *Sp;
     cudaSetDevice(S.device);
+#if defined(__linux__)
+    prctl(PR_SET_TIMERSLACK, 1000UL, 0UL, 0UL, 0UL);  // short polling sleeps stay short
+#endif
     std::deque<std::shared_ptr<ServeReq>> queue;      // admission order
     std::vector<std::shared_ptr<ServeReq>> finished;  // to hand back under the lock
     for (;;) {
@@ -672,6 +535,10 @@ pf_status pf_serve_start(pf_ctx *ctx, const pf_serve_config *cfg) {
     if (ctx->serve) return ctx->fail(PF_EBUSY, "already serving");
     if (!cfg) return ctx->fail(PF_EINVAL, "null config");
     pf_serve_config c = *cfg;
+    if (c.mode != PF_SERVE_BATCHED && c.mode != PF_SERVE_DEVICE_LOOP)
+        return ctx->fail(PF_EINVAL, "serve mode must be PF_SERVE_BATCHED or PF_SERVE_DEVICE_LOOP");
+    if (c.batch_pairs < 0 || c.overlap_pairs < 0)
+        return ctx->fail(PF_EINVAL, "batch_pairs or overlap_pairs < 0");
     if (c.max_requests == 0) c.max_requests = 256;
     if (c.chunk_pairs == 0) c.chunk_pairs = kServeMaxChunk;
     if (c.idle_exit_us == 0) c.idle_exit_us = 500;
@@ -694,11 +561,26 @@ pf_status pf_serve_start(pf_ctx *ctx, const pf_serve_config *cfg) {
     budget &= ~size_t(255);
     auto S = new ServeState();
     S->cfg = c;
+    S->ctx = ctx;
     S->device = ctx->device;
     S->budget = budget;
     // pinned staging: ~20 B per pair against ~370 B per pair on the device
     S->stage_budget = std::max<size_t>(budget / 16, size_t(64) << 20) & ~size_t(255);
     S->paused = c.start_paused != 0;
+    if (c.mode == PF_SERVE_BATCHED) {
+        bool ok = cudaHostAlloc(&S->stage_mem, S->stage_budget, cudaHostAllocMapped) == cudaSuccess;
+        pf_status st = ok ? batch_start(ctx, S) : ctx->fail(PF_ENOMEM, "serve staging allocation");
+        if (st != PF_OK) {
+            cudaGetLastError();
+            ctx->serve = S;
+            pf_serve_stop(ctx);
+            return st;
+        }
+        S->host_arena.reset(S->stage_budget);
+        ctx->serve = S;
+        S->th = std::thread(batch_scheduler, S);
+        return PF_OK;
+    }
     bool ok = cudaMalloc(&S->arena, budget) == cudaSuccess &&
               cudaMalloc(&S->d_desc, sizeof(ServeDesc) * c.max_requests) == cudaSuccess &&
               cudaMalloc(&S->d_done, sizeof(unsigned) * c.max_requests) == cudaSuccess &&
@@ -775,9 +657,15 @@ pf_status pf_submit(pf_ctx *ctx, const pf_request *req, uint64_t *ticket) {
                                           !req->accept || !req->count || !req->dist)))
         return ctx->fail(PF_EINVAL, "malformed request: null pointer");
     bool bad_off = false, bad_E = false;
+    int64_t longest = 0;
+    int emax = 0;
     for (int64_t p = 0; p < req->n; ++p) {
-        bad_off |= req->byte_off[p + 1] < req->byte_off[p];
-        bad_E |= (req->E[p] < 0) | (req->E[p] > PF_MAX_E);
+        const int64_t len = req->byte_off[p + 1] - req->byte_off[p];
+        const int e = req->E[p];
+        bad_off |= len < 0;
+        bad_E |= (e < 0) | (e > PF_MAX_E);
+        longest = std::max(longest, len);
+        emax = std::max(emax, e);
     }
     if (bad_off) return ctx->fail(PF_EINVAL, "malformed request: offsets decrease");
     if (bad_E) return ctx->fail(PF_EINVAL, "malformed request: E outside [0, %d]", PF_MAX_E);
@@ -785,6 +673,23 @@ pf_status pf_submit(pf_ctx *ctx, const pf_request *req, uint64_t *ticket) {
     const int64_t words = (tb >> 5) + req->n + 1;
     auto q = std::make_shared<ServeReq>();
     q->req = *req;
+    q->E_max = emax;
+    q->longest = longest;
+    if (S->bp) {  // batched mode: requests stream through the batch buffers
+        const pf_status st = batch_prepare(ctx, S, q.get());
+        if (st != PF_OK) return st;
+        q->t_submit = std::chrono::steady_clock::now();
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            q->ticket = S->next_ticket++;
+            S->pending.push_back(q);
+            S->reqs[q->ticket] = q;
+            S->stats.submitted++;
+        }
+        S->cv_work.notify_all();
+        *ticket = q->ticket;
+        return PF_OK;
+    }
     q->total_bytes = req->n ? req->byte_off[req->n] - req->byte_off[0] : 0;
     q->total_words = words;
     q->nchunks = (int)((req->n + S->cfg.chunk_pairs - 1) / S->cfg.chunk_pairs);
@@ -867,6 +772,12 @@ pf_status pf_serve_replay(pf_ctx *ctx, const pf_request *pool, int npool,
             return ctx->fail(PF_EINVAL, "pf_serve_replay: arrival times decrease");
     using clk = std::chrono::steady_clock;
     std::vector<uint64_t> tickets((size_t)count, 0);
+#if defined(__linux__)
+    // arrivals are paced by short sleeps: tighten the calling thread's timer
+    // slack for the replay, and give it back afterwards
+    const int slack = prctl(PR_GET_TIMERSLACK, 0UL, 0UL, 0UL, 0UL);
+    prctl(PR_SET_TIMERSLACK, 1000UL, 0UL, 0UL, 0UL);
+#endif
     const auto t0 = clk::now();
     pf_status first = PF_OK;
     for (int i = 0; i < count; ++i) {
@@ -888,6 +799,9 @@ pf_status pf_serve_replay(pf_ctx *ctx, const pf_request *pool, int npool,
         if (st != PF_OK && first == PF_OK) first = st;
     }
     if (elapsed_s) *elapsed_s = std::chrono::duration<double>(clk::now() - t0).count();
+#if defined(__linux__)
+    if (slack > 0) prctl(PR_SET_TIMERSLACK, (unsigned long)slack, 0UL, 0UL, 0UL);
+#endif
     return first;
 }
 
@@ -903,6 +817,7 @@ pf_status pf_serve_stop(pf_ctx *ctx) {
     }
     S->cv_work.notify_all();
     if (S->th.joinable()) S->th.join();
+    if (S->bp) batch_stop(S);
     if (S->s_loop) cudaStreamSynchronize(S->s_loop);
     if (S->s_copy) cudaStreamSynchronize(S->s_copy);
     {

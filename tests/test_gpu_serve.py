@@ -1,10 +1,13 @@
-"""Serving (continuous batching over the device loop) through the C ABI.
+"""Serving (continuous batching) through the C ABI, in both modes: device
+batches running the tuned path (PF_SERVE_BATCHED) and the device-resident
+loop (PF_SERVE_DEVICE_LOOP).
 
 Results must be bit-exact with the oracle, identical for a request served
 alone and in a mix of concurrent requests, correct when the memory budget
-admits one request at a time; malformed requests are refused on the host;
-waits are bounded (timeouts, cancellation on stop, the device loop leaving
-when idle and coming back on demand).
+admits one request at a time (device loop) or splits requests across
+batches (batched); malformed requests are refused on the host; waits are
+bounded (timeouts, cancellation on stop, the device loop leaving when idle
+and coming back on demand).
 """
 import threading
 import time
@@ -33,9 +36,12 @@ def ctx(pf):
     pf.pf_destroy(c)
 
 
-def make_request(pf, seed, n, deciders=3, p0=0):
+MODES = [0, 1]   # PF_SERVE_BATCHED, PF_SERVE_DEVICE_LOOP
+
+
+def make_request(pf, seed, n, deciders=3, p0=0, pinned=False):
     P = synth.generate(synth.SERVE, seed, n, kmax=60, p0=p0)
-    return P, pf.Request(deciders, P.reads, P.refs, P.read_off, P.E)
+    return P, pf.Request(deciders, P.reads, P.refs, P.read_off, P.E, pinned=pinned)
 
 
 def expected(P, deciders):
@@ -52,8 +58,9 @@ def check(P, R, deciders):
     assert np.array_equal(R.dist[:P.n], d)
 
 
-def test_requests_bit_exact(pf, ctx):
-    pf.pf_serve_start(ctx, chunk_pairs=512)
+@pytest.mark.parametrize("mode", MODES)
+def test_requests_bit_exact(pf, ctx, mode):
+    pf.pf_serve_start(ctx, chunk_pairs=512, mode=mode)
     reqs = [make_request(pf, 100 + i, n, deciders=d)
             for i, (n, d) in enumerate([(1000, 3), (5000, 1), (777, 2), (20000, 3), (1, 3), (0, 3)])]
     for _, R in reqs:
@@ -67,8 +74,9 @@ def test_requests_bit_exact(pf, ctx):
     pf.pf_serve_stop(ctx)
 
 
-def test_alone_and_in_the_mix_are_identical(pf, ctx):
-    pf.pf_serve_start(ctx, chunk_pairs=256)
+@pytest.mark.parametrize("mode", MODES)
+def test_alone_and_in_the_mix_are_identical(pf, ctx, mode):
+    pf.pf_serve_start(ctx, chunk_pairs=256, mode=mode)
     P, alone = make_request(pf, 7, 6000)
     pf.pf_submit(ctx, alone)
     assert pf.pf_wait(ctx, alone.ticket, 60000)[0] == 0
@@ -89,9 +97,12 @@ def test_alone_and_in_the_mix_are_identical(pf, ctx):
     pf.pf_serve_stop(ctx)
 
 
-def test_budget_admits_one_request_at_a_time(pf, ctx):
-    # room for two 20k-pair requests at most: the others wait for memory
-    pf.pf_serve_start(ctx, hbm_budget=24 << 20, max_requests=8, chunk_pairs=1024)
+@pytest.mark.parametrize("mode", MODES)
+def test_budget_admits_one_request_at_a_time(pf, ctx, mode):
+    # device loop: room for two 20k-pair requests at most, the others wait
+    # for memory; batched: batches of about 15k pairs, so every request is
+    # split across two or three of them
+    pf.pf_serve_start(ctx, hbm_budget=24 << 20, max_requests=8, chunk_pairs=1024, mode=mode)
     reqs = [make_request(pf, 300 + i, 20000) for i in range(5)]
     for _, R in reqs:
         pf.pf_submit(ctx, R)
@@ -101,8 +112,9 @@ def test_budget_admits_one_request_at_a_time(pf, ctx):
     pf.pf_serve_stop(ctx)
 
 
-def test_malformed_requests_are_refused(pf, ctx):
-    pf.pf_serve_start(ctx, hbm_budget=8 << 20)
+@pytest.mark.parametrize("mode", MODES)
+def test_malformed_requests_are_refused(pf, ctx, mode):
+    pf.pf_serve_start(ctx, hbm_budget=8 << 20, mode=mode)
     P, R = make_request(pf, 5, 100)
     bad_E = pf.Request(3, P.reads, P.refs, P.read_off, np.full(100, 40, np.int16))
     with pytest.raises(pf.PFError) as ei:
@@ -114,29 +126,44 @@ def test_malformed_requests_are_refused(pf, ctx):
     with pytest.raises(pf.PFError) as ei:
         pf.pf_submit(ctx, bad_off)
     assert ei.value.status == 1
-    P2, big = make_request(pf, 6, 100000)   # cannot fit 8 MiB
-    with pytest.raises(pf.PFError) as ei:
+    P2, big = make_request(pf, 6, 100000)
+    if mode == 1:                              # cannot fit 8 MiB whole
+        with pytest.raises(pf.PFError) as ei:
+            pf.pf_submit(ctx, big)
+        assert ei.value.status == 2
+    else:                                      # streams through the batches
         pf.pf_submit(ctx, big)
-    assert ei.value.status == 2
+        assert pf.pf_wait(ctx, big.ticket, 120000)[0] == 0
+        check(P2, big, 3)
     pf.pf_submit(ctx, R)                       # the serving loop is unaffected
     assert pf.pf_wait(ctx, R.ticket, 60000)[0] == 0
     check(P, R, 3)
     pf.pf_serve_stop(ctx)
 
 
-def test_invalid_bytes_report_edata(pf, ctx):
-    pf.pf_serve_start(ctx)
+@pytest.mark.parametrize("mode", MODES)
+def test_invalid_bytes_report_edata(pf, ctx, mode):
+    # paused, so that the bad request and a good one share a batch: the
+    # error belongs to the request whose bytes carried it
+    pf.pf_serve_start(ctx, mode=mode, start_paused=True)
     P, _ = make_request(pf, 8, 500)
     reads = P.reads.copy()
     reads[10] = ord("X")
     R = pf.Request(3, reads, P.refs, P.read_off, P.E)
+    P2, good = make_request(pf, 12, 700)
     pf.pf_submit(ctx, R)
+    pf.pf_submit(ctx, good)
+    time.sleep(0.05)
+    pf.pf_serve_resume(ctx)
     assert pf.pf_wait(ctx, R.ticket, 60000)[0] == 7
+    assert pf.pf_wait(ctx, good.ticket, 60000)[0] == 0
+    check(P2, good, 3)
     pf.pf_serve_stop(ctx)
 
 
-def test_paused_wait_times_out_and_stop_cancels(pf, ctx):
-    pf.pf_serve_start(ctx, start_paused=True)
+@pytest.mark.parametrize("mode", MODES)
+def test_paused_wait_times_out_and_stop_cancels(pf, ctx, mode):
+    pf.pf_serve_start(ctx, start_paused=True, mode=mode)
     P, R = make_request(pf, 9, 3000)
     pf.pf_submit(ctx, R)
     st, _ = pf.pf_wait(ctx, R.ticket, 200)
@@ -152,7 +179,7 @@ def test_paused_wait_times_out_and_stop_cancels(pf, ctx):
 
 
 def test_device_loop_leaves_when_idle_and_returns(pf, ctx):
-    pf.pf_serve_start(ctx, idle_exit_us=1000)
+    pf.pf_serve_start(ctx, idle_exit_us=1000, mode=1)
     P1, R1 = make_request(pf, 10, 2000)
     pf.pf_submit(ctx, R1)
     assert pf.pf_wait(ctx, R1.ticket, 60000)[0] == 0
@@ -166,8 +193,9 @@ def test_device_loop_leaves_when_idle_and_returns(pf, ctx):
     pf.pf_serve_stop(ctx)
 
 
-def test_replay_open_loop_load(pf, ctx):
-    pf.pf_serve_start(ctx)
+@pytest.mark.parametrize("mode", MODES)
+def test_replay_open_loop_load(pf, ctx, mode):
+    pf.pf_serve_start(ctx, mode=mode)
     pool = [make_request(pf, 400 + i, n) for i, n in enumerate((1000, 4000, 12000))]
     arrivals = np.cumsum(np.random.default_rng(1).exponential(0.002, size=30))
     st, lat, el = pf.pf_serve_replay(ctx, [R for _, R in pool], arrivals)
@@ -175,3 +203,50 @@ def test_replay_open_loop_load(pf, ctx):
     for P, R in pool:
         check(P, R, 3)
     pf.pf_serve_stop(ctx)
+
+
+# ---- batched mode ------------------------------------------------------------
+
+@pytest.mark.parametrize("pinned", [False, True])
+def test_batched_splits_requests_and_mixes_deciders(pf, ctx, pinned):
+    # batches of 1,000 pairs at most: every request below is split across
+    # several batches, and the decider sets 1, 2 and 3 share batches
+    pf.pf_serve_start(ctx, mode=0, batch_pairs=1000, start_paused=True)
+    reqs = [make_request(pf, 500 + i, n, deciders=d, pinned=pinned)
+            for i, (n, d) in enumerate([(2500, 3), (700, 2), (1, 1), (3001, 1), (999, 2),
+                                        (1000, 3), (0, 3), (4321, 2)])]
+    for _, R in reqs:
+        pf.pf_submit(ctx, R)
+    pf.pf_serve_resume(ctx)
+    for P, R in reqs:
+        assert pf.pf_wait(ctx, R.ticket, 60000)[0] == 0
+        check(P, R, R.deciders)
+    assert pf.pf_serve_stats_get(ctx)["loop_launches"] >= 13
+    pf.pf_serve_stop(ctx)
+
+
+def test_batched_pinned_and_pageable_agree(pf, ctx):
+    pf.pf_serve_start(ctx, mode=0)
+    P, a = make_request(pf, 77, 9000, pinned=True)
+    _, b = make_request(pf, 77, 9000, pinned=False)
+    pf.pf_submit(ctx, a)
+    pf.pf_submit(ctx, b)
+    assert pf.pf_wait(ctx, a.ticket, 60000)[0] == 0
+    assert pf.pf_wait(ctx, b.ticket, 60000)[0] == 0
+    for x, y in ((a.accept, b.accept), (a.count, b.count), (a.dist, b.dist)):
+        assert np.array_equal(x, y)
+    check(P, a, 3)
+    pf.pf_serve_stop(ctx)
+
+
+def test_batched_uses_the_serving_contexts_tuning(pf, ctx):
+    # the plain kernel below the small-batch size, the scheduler above it:
+    # both give the oracle's results
+    for small in (0, 1 << 30):
+        pf.pf_set_small_batch(ctx, small)
+        pf.pf_serve_start(ctx, mode=0)
+        P, R = make_request(pf, 90, 5000)
+        pf.pf_submit(ctx, R)
+        assert pf.pf_wait(ctx, R.ticket, 60000)[0] == 0
+        check(P, R, 3)
+        pf.pf_serve_stop(ctx)
