@@ -150,6 +150,29 @@ def oracle_step_rate(n_sample, threads=None):
     return n_sample / dt, dt, threads
 
 
+def needed_ops_per_pair(n_sample):
+    """Integer operations the method needs per pair on average, counted on
+    the first n_sample pairs of the workload by the oracle's work counters
+    (part of the CPU-baseline leg): the per-word figures of the full count,
+    applied to the words each decider needs before it is decided (a
+    word-parallel kernel stops a pair once both are).  Returns (ops, what)."""
+    import oracle
+    import synth
+    P = synth.generate(synth.SKEWED, SEED, n_sample, m=M, E=E_HEAD, kmax=KMAX)
+    w = oracle.work_batch(P).astype(np.int64)
+    D = 2 * E_HEAD + 1
+    words = lambda cols: (cols + 31) // 32
+    w_map = words(np.maximum(w[:, 1], w[:, 3]))
+    w_and, w_ham = words(w[:, 3]), words(w[:, 2])
+    ops = (5 * D * w_map + 5 * np.maximum(w_ham - w_map, 0)   # map (d = 0 alone past it)
+           + 8 * D * w_and + w_ham                            # GateKeeper
+           + (3 * D + 1) * w[:, 0])                           # SneakySnake searches
+    what = ("oracle work counts on pairs 0..%d: SneakySnake %.2f search-words, map %.2f "
+            "words, GateKeeper AND %.2f words, Hamming %.2f words per pair"
+            % (n_sample, w[:, 0].mean(), w_map.mean(), w_and.mean(), w_ham.mean()))
+    return float(ops.mean()), what
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -776,6 +799,17 @@ def main_gpu(args):
                 "traffic": None, "peak_source": pk_kind}
     roof["ms_per_launch"] = ms_dom
     roof["sm_mhz_during_step"] = sm_mhz
+    if roof["bound"] == "alu":
+        # the same peak measured: a LOP3 + funnel-shift loop on every SM
+        clk_pk = Clocks(local)
+        clk_pk.start()
+        pk_ops, pk_ms = pf.pf_peak_int(ctx, 0, 30)
+        pk_clk = clk_pk.stop()
+        roof["peak_measured"] = pk_ops / 1e12
+        roof["frac_of_measured"] = roof["achieved"] / roof["peak_measured"]
+        roof["peak_measured_source"] = ("pf_peak_int kind 0 (LOP3 + SHF, full occupancy), "
+                                        "%.1f ms per launch x 30, SM clock median %s MHz"
+                                        % (pk_ms, pk_clk.get("sm_mhz")))
 
     total = n * world
     value = total / (ms / 1000.0)
@@ -815,6 +849,11 @@ def main_gpu(args):
     if rank == 0 and world == 1 and not args.no_cpu:
         r, dt, thr = oracle_step_rate(args.cpu_sample)
         r1, dt1, _ = oracle_step_rate(args.cpu_sample_1t, threads=1)
+        if roof["bound"] == "alu" and dominant == "filter":
+            need, sample = needed_ops_per_pair(args.work_sample)
+            roof["ops_per_pair_needed"] = need
+            roof["frac_needed"] = n * need / (ms_dom / 1000.0) / 1e12 / roof["peak"]
+            roof["needed_sample"] = sample
         line["cpu_baseline"] = {"value": r, "unit": "pairs/s", "cores": thr, "kind": "oracle",
                                 "sample": "first %d pairs of the workload (filter both "
                                           "deciders + banded WF on SneakySnake accepts), "
@@ -843,6 +882,8 @@ def main():
                     help="pairs of the oracle's timed sample for cpu_baseline (about 10 s)")
     ap.add_argument("--cpu-sample-1t", type=int, default=300_000,
                     help="pairs of the single-thread oracle sample (about 5 s)")
+    ap.add_argument("--work-sample", type=int, default=200_000,
+                    help="pairs of the oracle work-count sample for roofline.frac_needed")
     ap.add_argument("--ref-sample", type=int, default=400_000,
                     help="pairs per step of --impl reference (K + W steps in a few minutes)")
     ap.add_argument("--no-cpu", action="store_true")

@@ -552,3 +552,46 @@ def test_false_reject_examples_are_the_shortest(kind, L, E_first):
             else:
                 c = oracle.int_batch("shouji", P)
             assert not np.any((ed <= E) & (c > E)), (length, E)
+
+
+# ---- work counts (needed-work roofline; they change no result) --------------
+
+def test_work_counts_worked_example(golden):
+    kv, _ = golden("sneakysnake_example.txt")
+    F, R, E = kv["reference"], kv["read"], int(kv["E"])
+    # Counted by hand on the map of Fig. 8.1/8.2 (12 columns, one word):
+    # three deepest-pipe searches (from columns 0, 5 and 10; each ends at an
+    # obstacle: columns 4, 9 and 11), so the walk reads all 12 columns.
+    # The d = 0 row mismatches at columns 4..11: the Hamming count passes
+    # E = 3 at column 7 (8 columns read).  GateKeeper accepts (count 2), so
+    # its AND needs every column.
+    assert oracle.work_counts(R, F, E) == (3, 12, 8, 12)
+    assert oracle.sneakysnake(R, F, E) == 3 and oracle.gatekeeper(R, F, E) == 2
+
+
+def test_work_counts_are_the_walks_searches():
+    # one-word pairs: the walk searches once per obstacle, plus once to leave
+    # the grid unless an obstacle step already did; a rejected pair stops at
+    # its (E+1)-th obstacle.  Identical pairs need one search and, with the
+    # Hamming check accepting, no amended AND.
+    rng = np.random.default_rng(11)
+    for _ in range(400):
+        m = int(rng.integers(1, 33))
+        E = int(rng.integers(0, 6))
+        R = bytes(int(x) for x in rng.choice(list(b"ACGT"), m))
+        F = bytearray(R)
+        for _ in range(int(rng.integers(0, 8))):
+            F[int(rng.integers(0, m))] = int(rng.choice(list(b"ACGT")))
+        F = bytes(F)
+        words, cols, ham_cols, and_cols = oracle.work_counts(R, F, E)
+        k = oracle.sneakysnake(R, F, E)
+        if k > E:
+            assert words == E + 1
+        else:
+            assert words in (k, k + 1) and cols == m
+        h = oracle.hamming(R, F)
+        assert ham_cols == (m if h <= E else
+                            1 + next(i for i in range(m)
+                                     if sum(R[j] != F[j] for j in range(i + 1)) > E))
+        assert (and_cols == 0) == (h <= E)
+    assert oracle.work_counts("ACGTACGT", "ACGTACGT", 2) == (1, 8, 8, 0)
