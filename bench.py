@@ -285,7 +285,7 @@ def serve_reference_rates(pf, ctx, seed, n=4_000_000):
 
 def serve_measure(pf, ctx, seconds_per_load, seed, mode=0, ref=None, loads=(0.25, 0.5, 0.9)):
     """Serving through pf_serve_replay.  Peak = pairs/s of a burst of every
-    request of the pool (four times over) submitted at once; then Poisson
+    request of the pool (16 times over, about 25M pairs) submitted at once; then Poisson
     arrivals at fractions of that peak and, when it is below the peak, at a
     quarter of the batched path's device throughput (ref).  Latency = submit
     to results in host memory."""
@@ -293,9 +293,9 @@ def serve_measure(pf, ctx, seconds_per_load, seed, mode=0, ref=None, loads=(0.25
     mean_pairs = float(sizes.mean())
     pf.pf_serve_start(ctx, mode=mode)
     pf.pf_serve_replay(ctx, pool[:8], np.zeros(8))           # warm-up
-    burst = np.zeros(4 * len(pool))
+    burst = np.zeros(16 * len(pool))
     st, lat, el = pf.pf_serve_replay(ctx, pool, burst)
-    peak = 4 * float(sizes.sum()) / el
+    peak = 16 * float(sizes.sum()) / el
     out = {"mode": "batched" if mode == 0 else "device_loop", "peak_pairs_s": peak,
            "requests_pool": len(pool), "mean_request_pairs": mean_pairs, "status": int(st),
            "buffers": "page-locked host"}

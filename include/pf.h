@@ -427,7 +427,7 @@ typedef struct {
                             pf_serve_resume */
     int mode;            /* PF_SERVE_BATCHED or PF_SERVE_DEVICE_LOOP */
     int batch_pairs;     /* batched: most pairs in one device batch, 0 = up
-                            to 2^22 as the budget allows; >= 1 */
+                            to 2^20 as the budget allows; >= 0 */
     int overlap_pairs;   /* batched: while a batch runs, the next one is
                             launched beside it only once it holds this many
                             pairs (else it keeps growing until the GPU has
@@ -512,6 +512,23 @@ PF_API pf_status pf_serve_stats_get(pf_ctx *ctx, pf_serve_stats *out);
 PF_API pf_status pf_serve_replay(pf_ctx *ctx, const pf_request *pool, int npool,
                                  const double *arrival_s, int count, double *latency_ms,
                                  double *elapsed_s);
+
+/* Batched mode: the most recent device batches (up to the last 65,536),
+ * oldest first, PF_SERVE_TRACE_FIELDS doubles each, into records (host,
+ * cap records; *count receives how many were written):
+ *   [0] launch time and [1] completion time (seconds since pf_serve_start,
+ *       on the scheduler thread's clock: when it enqueued the batch and
+ *       when it saw the batch finish),
+ *   [2] pairs, [3] request parts,
+ *   [4] ms the batch's GPU work waited for its uploads and for the batch
+ *       before it (from its enqueue on the compute stream to its start),
+ *   [5] ms of GPU work (start of its first kernel to end of its last),
+ *   [6] ms the scheduler spent enqueuing it, [7] its decider set,
+ *   [8..12] ms of GPU work in its phases: offsets, packing, filter,
+ *       compaction and verification, epilogue.
+ * PF_EBUSY when not serving in the batched mode. */
+#define PF_SERVE_TRACE_FIELDS 13
+PF_API pf_status pf_serve_trace(pf_ctx *ctx, double *records, int cap, int *count);
 
 /* Stop the device loop and the scheduler; requests not finished end with
  * PF_ECANCELLED. */

@@ -25,6 +25,7 @@ __all__ = [
     "pf_filter_partitioned", "pf_filter_shouji", "pf_filter_shd", "PF_SHD_VACANT_ZERO",
     "PF_SHD_STREAK", "pf_set_small_batch", "pf_tune_batch", "pf_set_resolve_by_bounds",
     "pf_last_verified_count", "pf_peak_int", "PF_SERVE_BATCHED", "PF_SERVE_DEVICE_LOOP",
+    "pf_serve_trace",
 ]
 
 PF_SNEAKYSNAKE = 1
@@ -130,6 +131,7 @@ def load():
         "pf_serve_resume": [P],
         "pf_serve_stats_get": [P, ctypes.POINTER(ServeStats)],
         "pf_serve_stop": [P],
+        "pf_serve_trace": [P, P, I, ctypes.POINTER(ctypes.c_int)],
         "pf_run_host": [P, U, P, P, P, I, P, I, P, P, P, I64, I64],
         "pf_serve_replay": [P, P, I, P, I, P, ctypes.POINTER(ctypes.c_double)],
         "pf_tune_set": [P, U, I, I, I],
@@ -587,6 +589,19 @@ def pf_serve_stats_get(ctx):
     st = ServeStats()
     _check(load().pf_serve_stats_get(ctx.handle, ctypes.byref(st)), ctx.handle)
     return {f: getattr(st, f) for f, _ in ServeStats._fields_}
+
+
+def pf_serve_trace(ctx, cap=65536):
+    """Batched mode: the most recent device batches as a float64 array of
+    shape (k, 13): launch s, completion s, pairs, request parts, ms waiting
+    for uploads / the previous batch, GPU ms, enqueue ms, decider set, GPU ms
+    of the offsets, pack, filter, compaction + verification and epilogue."""
+    import numpy as np
+    out = np.zeros((max(cap, 1), 13), dtype=np.float64)
+    k = ctypes.c_int()
+    _check(load().pf_serve_trace(ctx.handle, ctypes.c_void_p(out.ctypes.data), int(cap),
+                                 ctypes.byref(k)), ctx.handle)
+    return out[:k.value]
 
 
 def pf_serve_stop(ctx):

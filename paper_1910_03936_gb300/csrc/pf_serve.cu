@@ -805,6 +805,15 @@ pf_status pf_serve_replay(pf_ctx *ctx, const pf_request *pool, int npool,
     return first;
 }
 
+pf_status pf_serve_trace(pf_ctx *ctx, double *records, int cap, int *count) {
+    if (!ctx) return PF_EINVAL;
+    ServeState *S = ctx->serve;
+    if (!S || !S->bp) return ctx->fail(PF_EBUSY, "not serving in the batched mode");
+    if (!count || cap < 0 || (cap > 0 && !records))
+        return ctx->fail(PF_EINVAL, "pf_serve_trace: bad arguments");
+    return batch_trace(S, records, cap, count);
+}
+
 pf_status pf_serve_stop(pf_ctx *ctx) {
     if (!ctx) return PF_EINVAL;
     ServeState *S = ctx->serve;

@@ -80,8 +80,8 @@ struct ServeReq {
     int E_max = 0;                 // the largest threshold of its pairs
     int64_t longest = 0;           // its longest pair, bytes
     bool admitted = false;
-    // device-visible views of its per-pair arrays: the caller's page-locked
-    // buffers themselves, or (pageable ones) pinned staging copies
+    // device-visible views: page-locked inputs read in place (else copied
+    // into the batch slot), outputs written in place (else pinned staging)
     const int64_t *d_boff = nullptr;
     const int16_t *d_E = nullptr;
     uint8_t *d_acc = nullptr;
@@ -181,5 +181,6 @@ pf_status batch_start(pf_ctx *ctx, ServeState *S);
 pf_status batch_prepare(pf_ctx *ctx, ServeState *S, ServeReq *q);
 void batch_scheduler(ServeState *S);
 void batch_stop(ServeState *S);
+pf_status batch_trace(ServeState *S, double *records, int cap, int *count);
 
 }  // namespace pf

@@ -13,13 +13,17 @@
 // the other on the serving context's stream, so a batch's epilogue has read
 // its outputs before the next batch's offsets kernel overwrites them.
 //
-// A batch on the GPU: wait for its uploads; upload the segment table; the
-// offsets kernel turns the parts' byte offsets (read in place from the
-// requests' page-locked arrays, or their pinned staging copies) into the
-// batch's byte and word offsets, lengths and thresholds; both planes are
-// packed; the scheduler's binned filter, compaction and verification run as
-// in pf_filter_verify; the epilogue writes every pair's results into its
-// request's buffers in the request's own output layout.
+// A batch on the GPU: wait for its uploads (every part's bytes, the segment
+// table, and the byte offsets and thresholds of pageable requests: all on
+// the copy stream, since a copy issued on the compute stream would queue in
+// the copy engine behind later batches' uploads); the offsets kernel turns
+// the parts' byte offsets (page-locked ones read in place, which spares the
+// copy engine two small transfers per part) into the batch's byte and word
+// offsets, lengths and thresholds; both planes are packed; the scheduler's binned filter,
+// compaction and verification run as in pf_filter_verify; the epilogue
+// writes every pair's results into its request's buffers in the request's
+// own output layout (directly when they are page-locked: 10 bytes per pair
+// of posted writes).
 #include <algorithm>
 #include <cstring>
 #if defined(__linux__)
@@ -33,8 +37,12 @@ namespace pf {
 namespace {
 
 constexpr int kMaxSegs = 1024;          // request parts per batch
-constexpr int kBatchSlots = 3;          // two batches on the GPU, one filling
-constexpr int64_t kDefaultBatchPairs = int64_t(1) << 22;
+constexpr int kBatchSlots = 4;          // two batches on the GPU, up to two filling
+// Batches of up to 2^20 pairs: larger ones raise a burst's throughput
+// little (the uploads bind) and lengthen the latency of every request they
+// hold (measured: p99 at 73% of the host-link bound 14 ms with 2^20, 31 ms
+// with 2^22).
+constexpr int64_t kDefaultBatchPairs = int64_t(1) << 20;
 constexpr int64_t kBytesPerPairCap = 200;  // byte area per pair of capacity, per side
 constexpr unsigned kErrLaunch = 1u << 30;   // a batch whose launch failed
 // Default of overlap_pairs: a second batch joins the one on the GPU only
@@ -42,13 +50,15 @@ constexpr unsigned kErrLaunch = 1u << 30;   // a batch whose launch failed
 // and grow meanwhile (a batch costs about 0.2 ms of fixed latency, its
 // chain of launches).
 constexpr int64_t kOverlapPairs = int64_t(1) << 18;
+constexpr uint64_t kTraceCap = 65536;   // batches kept by the trace
+constexpr int kOffsetsIlp = 4;          // positions per thread and round, offsets kernel
 
 // One request part in a batch: pairs [a, a + n) of the request are batch
 // positions [p0, p0 + n); their bytes start at bbase in the slot's areas.
 struct SegDesc {
     int64_t p0, n, a, bbase, req_n;
-    const int64_t *boff;   // request byte offsets (device-visible)
-    const int16_t *E;      // request thresholds (device-visible)
+    const int64_t *boff;   // the part's n + 1 byte offsets (device-visible)
+    const int16_t *E;      // the part's n thresholds (device-visible)
     uint8_t *acc;          // request outputs (device-visible)
     int16_t *cnt;
     int32_t *dist;
@@ -68,29 +78,55 @@ __device__ __forceinline__ int seg_of_pos(const int64_t *sp0, int nseg, int64_t 
 
 // Byte offsets relative to the slot's areas (the parts are adjacent there),
 // word offsets floor(b / 32) + i (disjoint without a scan: sequence i ends
-// before floor(b_{i+1} / 32) + i + 1), lengths, thresholds and segment ids.
+// before floor(b_{i+1} / 32) + i + 1), lengths, thresholds and segment ids;
+// block 0 also clears the parts' error words for the packer.
 __global__ void __launch_bounds__(256)
 batch_offsets_kernel(const SegDesc *segs, int nseg, int64_t P, int64_t *boff, int64_t *woff,
-                     int32_t *lens, int16_t *E, int32_t *seg_of) {
+                     int32_t *lens, int16_t *E, int32_t *seg_of, unsigned *seg_err) {
     __shared__ int64_t sp0[kMaxSegs];
-    for (int k = threadIdx.x; k < nseg; k += blockDim.x) sp0[k] = segs[k].p0;
+    for (int k = threadIdx.x; k < nseg; k += blockDim.x) {
+        sp0[k] = segs[k].p0;
+        if (blockIdx.x == 0) seg_err[k] = 0u;
+    }
     __syncthreads();
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int s = seg_of_pos(sp0, nseg, i);
-        const SegDesc &d = segs[s];
-        const int64_t p = d.a + (i - d.p0);
-        const int64_t r0 = d.boff[d.a];
-        const int64_t b = d.boff[p] - r0 + d.bbase;
-        const int64_t e = d.boff[p + 1] - r0 + d.bbase;
-        boff[i] = b;
-        woff[i] = (b >> 5) + i;
-        lens[i] = (int32_t)(e - b);
-        E[i] = d.E[p];
-        seg_of[i] = s;
-        if (i == P - 1) {
-            boff[P] = e;
-            woff[P] = (e >> 5) + P;
+    // kOffsetsIlp positions per thread and round, all their loads issued
+    // before any is used: the offsets and thresholds of page-locked requests
+    // come over the host link, whose round trips a thread would otherwise
+    // wait out one by one
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < P;
+         i0 += stride * kOffsetsIlp) {
+        int sg[kOffsetsIlp];
+        int64_t r0[kOffsetsIlp], xb[kOffsetsIlp], xe[kOffsetsIlp], base[kOffsetsIlp];
+        int16_t th[kOffsetsIlp];
+#pragma unroll
+        for (int u = 0; u < kOffsetsIlp; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i >= P) continue;
+            sg[u] = seg_of_pos(sp0, nseg, i);
+            const SegDesc &d = segs[sg[u]];
+            const int64_t j = i - d.p0;
+            base[u] = d.bbase;
+            r0[u] = d.boff[0];
+            xb[u] = d.boff[j];
+            xe[u] = d.boff[j + 1];
+            th[u] = d.E[j];
+        }
+#pragma unroll
+        for (int u = 0; u < kOffsetsIlp; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i >= P) continue;
+            const int64_t b = xb[u] - r0[u] + base[u];
+            const int64_t e = xe[u] - r0[u] + base[u];
+            boff[i] = b;
+            woff[i] = (b >> 5) + i;
+            lens[i] = (int32_t)(e - b);
+            E[i] = th[u];
+            seg_of[i] = sg[u];
+            if (i == P - 1) {
+                boff[P] = e;
+                woff[P] = (e >> 5) + P;
+            }
         }
     }
 }
@@ -137,6 +173,8 @@ batch_epilogue_kernel(const SegDesc *segs, int nseg, int64_t P, unsigned bdec,
 
 struct BatchSlot {
     uint8_t *reads = nullptr, *refs = nullptr;  // device byte areas
+    int64_t *raw_off = nullptr;                  // parts' byte offsets, P + kMaxSegs
+    int16_t *raw_E = nullptr;                    // parts' thresholds, P
     SegDesc *h_segs = nullptr;                   // pinned
     SegDesc *d_segs = nullptr;                   // device
     unsigned *h_err = nullptr;                   // pinned, mapped: per-part error bits
@@ -148,7 +186,9 @@ struct BatchSlot {
     int E_max = 0;
     bool full = false;
     bool failed = false;  // its launch failed: nothing it holds is valid
-    cudaEvent_t ev_copied = nullptr, ev_start = nullptr, ev_done = nullptr;
+    cudaEvent_t ev_copied = nullptr, ev_enq = nullptr, ev_start = nullptr, ev_done = nullptr;
+    cudaEvent_t ev_phase[4] = {};       // after offsets, pack, filter, verification
+    double t_launch = 0, host_ms = 0;   // trace: scheduler clock, enqueue time
 
     void reset() {
         reqs.clear();
@@ -179,10 +219,16 @@ struct BatchPool {
     Scratch scr{};
     BatchSlot slots[kBatchSlots];
     std::deque<int> inflight;       // launched slots, in launch order
+    std::deque<int> ready;          // full slots waiting for the GPU, in order
     std::vector<int> free_slots;
     int open = -1;
     int admitted = 0;               // requests admitted and not finished
     int64_t overlap = kOverlapPairs;
+    // trace of the most recent batches (pf_serve_trace), a ring
+    std::mutex trace_mu;
+    std::vector<double> trace;      // kTraceCap records of PF_SERVE_TRACE_FIELDS
+    uint64_t trace_n = 0;           // records written so far
+    std::chrono::steady_clock::time_point t0;
 };
 
 namespace {
@@ -201,14 +247,11 @@ T *mapped(const T *p) {
     return static_cast<T *>(a.devicePointer);
 }
 
-// Pinned staging bytes a request needs: per-pair inputs when they are
-// pageable, outputs when they are.
+// Pinned staging bytes a request needs: its outputs, when they are
+// pageable (the GPU writes page-locked ones in place).
 size_t staging_need(const ServeReq &q) {
     const size_t n = (size_t)q.req.n, sl = (size_t)slots_of(q.req.deciders);
-    size_t b = 0;
-    if (!q.in_mapped) b += up256((n + 1) * 8) + up256(n * 2);
-    if (!q.out_mapped) b += up256(sl * n) + up256(sl * n * 2) + up256(n * 4);
-    return b;
+    return q.out_mapped ? 0 : up256(sl * n) + up256(sl * n * 2) + up256(n * 4);
 }
 
 // First placement of a request: staging (if any), device-visible views.
@@ -228,14 +271,6 @@ bool admit(ServeState &S, ServeReq &q) {
             o += up256(bytes);
             return p;
         };
-        if (!q.in_mapped) {
-            q.h_boff = reinterpret_cast<int64_t *>(take((n + 1) * 8));
-            q.h_E = reinterpret_cast<int16_t *>(take(n * 2));
-            std::memcpy(q.h_boff, q.req.byte_off, (n + 1) * 8);
-            if (n) std::memcpy(q.h_E, q.req.E, n * 2);
-            q.d_boff = mapped(q.h_boff);
-            q.d_E = mapped(q.h_E);
-        }
         if (!q.out_mapped) {
             q.h_acc = reinterpret_cast<uint8_t *>(take(sl * n));
             q.h_cnt = reinterpret_cast<int16_t *>(take(sl * n * 2));
@@ -267,7 +302,9 @@ int64_t fit(const BatchPool &B, const BatchSlot &b, const ServeReq &q) {
     return lo;
 }
 
-// Place k pairs of q into slot b and start their uploads.
+// Place k pairs of q into slot b and start their uploads: bytes, byte
+// offsets (k + 1, at raw_off + p0 + the part's index, so that every part
+// keeps its closing offset) and thresholds.
 void place(ServeState &S, BatchSlot &b, const std::shared_ptr<ServeReq> &qp, int64_t k) {
     BatchPool &B = *S.bp;
     ServeReq &q = *qp;
@@ -278,8 +315,19 @@ void place(ServeState &S, BatchSlot &b, const std::shared_ptr<ServeReq> &qp, int
     d.a = q.next;
     d.bbase = b.bytes;
     d.req_n = q.req.n;
-    d.boff = q.d_boff;
-    d.E = q.d_E;
+    if (q.in_mapped) {  // page-locked: the offsets kernel reads them in place
+        d.boff = q.d_boff + q.next;
+        d.E = q.d_E + q.next;
+    } else {
+        int64_t *off = b.raw_off + b.pairs + b.nseg;
+        int16_t *thr = b.raw_E + b.pairs;
+        d.boff = off;
+        d.E = thr;
+        cudaMemcpyAsync(off, q.req.byte_off + q.next, (size_t)(k + 1) * sizeof(int64_t),
+                        cudaMemcpyHostToDevice, B.s_copy);
+        cudaMemcpyAsync(thr, q.req.E + q.next, (size_t)k * sizeof(int16_t),
+                        cudaMemcpyHostToDevice, B.s_copy);
+    }
     d.acc = q.d_acc;
     d.cnt = q.d_cnt;
     d.dist = q.d_dist;
@@ -309,15 +357,20 @@ pf_status launch(ServeState &S, BatchSlot &b) {
     cudaStream_t st = B.s_compute;
     const int64_t P = b.pairs;
     const int ns = b.nseg;
+    // the segment table joins the batch's uploads on the copy stream: a copy
+    // issued on the compute stream would queue in the copy engine behind the
+    // uploads of later batches (milliseconds under load)
+    cudaMemcpyAsync(b.d_segs, b.h_segs, sizeof(SegDesc) * (size_t)ns, cudaMemcpyHostToDevice,
+                    B.s_copy);
+    cudaEventRecord(b.ev_enq, st);
     cudaEventRecord(b.ev_copied, B.s_copy);
     cudaStreamWaitEvent(st, b.ev_copied, 0);
     cudaEventRecord(b.ev_start, st);
-    cudaMemcpyAsync(b.d_segs, b.h_segs, sizeof(SegDesc) * (size_t)ns, cudaMemcpyHostToDevice, st);
-    cudaMemsetAsync(B.seg_err, 0, sizeof(unsigned) * (size_t)ns, st);
     const unsigned grid =
         (unsigned)std::max<int64_t>(1, std::min<int64_t>((P + 255) / 256, (int64_t)sub->sms * 8));
     batch_offsets_kernel<<<grid, 256, 0, st>>>(b.d_segs, ns, P, B.boff, B.woff, B.lens, B.E,
-                                               B.seg_of);
+                                               B.seg_of, B.seg_err);
+    cudaEventRecord(b.ev_phase[0], st);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
         e = launch_pack_ragged(b.reads, B.boff, B.woff, P, B.pl[0], B.pl[1], B.pl[2], sub->d_err,
@@ -326,6 +379,7 @@ pf_status launch(ServeState &S, BatchSlot &b) {
         e = launch_pack_ragged(b.refs, B.boff, B.woff, P, B.pl[3], B.pl[4], B.pl[5], sub->d_err,
                                st, B.seg_of, B.seg_err);
     if (e != cudaSuccess) return sub->cuda(e, "serve batch pack");
+    cudaEventRecord(b.ev_phase[1], st);
     PairsView pv;
     pv.read = SeqView{B.pl[0], B.pl[1], B.pl[2], B.woff, 0};
     pv.ref = SeqView{B.pl[3], B.pl[4], B.pl[5], B.woff, 0};
@@ -343,10 +397,12 @@ pf_status launch(ServeState &S, BatchSlot &b) {
     sub->stream = st;
     pf_status s = sub->run_filter(b.dec, a, B.scr);
     if (s != PF_OK) return s;
+    cudaEventRecord(b.ev_phase[2], st);
     e = launch_compact(a.need ? a.need : B.acc, P, B.scr.idx, B.scr.n_idx, B.scr.tiles, st);
     if (e == cudaSuccess)
         e = launch_verify(pv, B.lens, B.E, b.E_max, B.scr.idx, B.scr.n_idx, P, B.dist, sub->d_err,
                           sub->sms, st);
+    cudaEventRecord(b.ev_phase[3], st);
     if (e == cudaSuccess) {
         batch_epilogue_kernel<<<grid, 256, 0, st>>>(b.d_segs, ns, P, b.dec, B.seg_of, B.acc,
                                                     B.cnt, B.dist, B.E, B.seg_err, b.d_err_map);
@@ -406,7 +462,7 @@ pf_status batch_start(pf_ctx *ctx, ServeState *Sp) {
     // ids, outputs, scheduler scratch, planes) and the slots' byte areas
     const int64_t words_per_pair = kBytesPerPairCap / 32 + 2;
     const int64_t per_pair = 8 + 8 + 4 + 2 + 4 + 2 + 4 + 4 + 8 + 8 + 1 + 6 * 4 * words_per_pair +
-                             kBatchSlots * 2 * kBytesPerPairCap;
+                             kBatchSlots * (2 * kBytesPerPairCap + 8 + 2);
     int64_t P = S.cfg.batch_pairs ? S.cfg.batch_pairs : kDefaultBatchPairs;
     P = std::min<int64_t>(P, (int64_t)(S.budget / (size_t)per_pair));
     if (P < 1) return ctx->fail(PF_ENOMEM, "serve budget too small for one batch pair");
@@ -431,11 +487,14 @@ pf_status batch_start(pf_ctx *ctx, ServeState *Sp) {
                  o_bins = add((kNumBatchCfgs + 1) * 8), o_work = add(kNumBatchCfgs * 8),
                  o_hist = add(kNumBatchCfgs * 8), o_cur = add(kNumBatchCfgs * 8),
                  o_ident = add(4), o_need = add(nn);
-    size_t o_rd[kBatchSlots], o_rf[kBatchSlots], o_sg[kBatchSlots];
+    size_t o_rd[kBatchSlots], o_rf[kBatchSlots], o_sg[kBatchSlots], o_ro[kBatchSlots],
+        o_re[kBatchSlots];
     for (int i = 0; i < kBatchSlots; ++i) {
         o_rd[i] = add((size_t)B.B);
         o_rf[i] = add((size_t)B.B);
         o_sg[i] = add(sizeof(SegDesc) * kMaxSegs);
+        o_ro[i] = add((nn + kMaxSegs) * 8);
+        o_re[i] = add(nn * 2);
     }
     if (cudaMalloc(&B.mem, o) != cudaSuccess) {
         cudaGetLastError();
@@ -469,12 +528,19 @@ pf_status batch_start(pf_ctx *ctx, ServeState *Sp) {
         b.reads = reinterpret_cast<uint8_t *>(m + o_rd[i]);
         b.refs = reinterpret_cast<uint8_t *>(m + o_rf[i]);
         b.d_segs = reinterpret_cast<SegDesc *>(m + o_sg[i]);
+        b.raw_off = reinterpret_cast<int64_t *>(m + o_ro[i]);
+        b.raw_E = reinterpret_cast<int16_t *>(m + o_re[i]);
         void *dp = nullptr;
         ok = cudaHostAlloc(&b.h_segs, sizeof(SegDesc) * kMaxSegs, 0) == cudaSuccess &&
              cudaHostAlloc(&b.h_err, sizeof(unsigned) * kMaxSegs, cudaHostAllocMapped) ==
                  cudaSuccess &&
              cudaHostGetDevicePointer(&dp, b.h_err, 0) == cudaSuccess &&
              cudaEventCreateWithFlags(&b.ev_copied, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreate(&b.ev_enq) == cudaSuccess &&
+             cudaEventCreate(&b.ev_phase[0]) == cudaSuccess &&
+             cudaEventCreate(&b.ev_phase[1]) == cudaSuccess &&
+             cudaEventCreate(&b.ev_phase[2]) == cudaSuccess &&
+             cudaEventCreate(&b.ev_phase[3]) == cudaSuccess &&
              cudaEventCreate(&b.ev_start) == cudaSuccess &&
              cudaEventCreate(&b.ev_done) == cudaSuccess;
         b.d_err_map = static_cast<unsigned *>(dp);
@@ -496,6 +562,22 @@ pf_status batch_start(pf_ctx *ctx, ServeState *Sp) {
     // occupancy queries before the first batch
     for (int d = 1; d <= 3; ++d)
         for (int c = 0; c < kNumBatchCfgs; ++c) B.sub->grid_for(d, c);
+    B.trace.assign(kTraceCap * PF_SERVE_TRACE_FIELDS, 0.0);
+    B.t0 = std::chrono::steady_clock::now();
+    return PF_OK;
+}
+
+pf_status batch_trace(ServeState *Sp, double *records, int cap, int *count) {
+    BatchPool &B = *Sp->bp;
+    std::lock_guard<std::mutex> tl(B.trace_mu);
+    const uint64_t have = std::min<uint64_t>(B.trace_n, kTraceCap);
+    const uint64_t k = std::min<uint64_t>(have, (uint64_t)cap);
+    const uint64_t first = B.trace_n - k;   // the k most recent, oldest first
+    for (uint64_t i = 0; i < k; ++i)
+        std::memcpy(records + i * PF_SERVE_TRACE_FIELDS,
+                    &B.trace[((first + i) % kTraceCap) * PF_SERVE_TRACE_FIELDS],
+                    sizeof(double) * PF_SERVE_TRACE_FIELDS);
+    *count = (int)k;
     return PF_OK;
 }
 
@@ -584,9 +666,32 @@ void batch_scheduler(ServeState *Sp) {
                 S.fatal = "serve batch failed on the device";
                 b.failed = true;
             }
-            float ms = 0.f;
+            float ms = 0.f, wait_ms = 0.f;
             if (!b.failed && cudaEventElapsedTime(&ms, b.ev_start, b.ev_done) == cudaSuccess)
                 gpu_s += ms * 1e-3;
+            if (b.failed || cudaEventElapsedTime(&wait_ms, b.ev_enq, b.ev_start) != cudaSuccess)
+                wait_ms = -1.f;
+            {
+                std::lock_guard<std::mutex> tl(B.trace_mu);
+                double *r = &B.trace[(B.trace_n % kTraceCap) * PF_SERVE_TRACE_FIELDS];
+                r[0] = b.t_launch;
+                r[1] = std::chrono::duration<double>(clk::now() - B.t0).count();
+                r[2] = (double)b.pairs;
+                r[3] = (double)b.nseg;
+                r[4] = wait_ms;
+                r[5] = ms;
+                r[6] = b.host_ms;
+                r[7] = (double)b.dec;
+                cudaEvent_t marks[6] = {b.ev_start, b.ev_phase[0], b.ev_phase[1], b.ev_phase[2],
+                                        b.ev_phase[3], b.ev_done};
+                for (int k = 0; k < 5; ++k) {
+                    float pm = -1.f;
+                    if (b.failed || cudaEventElapsedTime(&pm, marks[k], marks[k + 1]) != cudaSuccess)
+                        pm = -1.f;
+                    r[8 + k] = pm;
+                }
+                B.trace_n++;
+            }
             complete(S, b, finished);
             B.free_slots.push_back(B.inflight.front());
             B.inflight.pop_front();
@@ -614,26 +719,42 @@ void batch_scheduler(ServeState *Sp) {
             }
             BatchSlot &b = B.slots[B.open];
             const int64_t k = b.full ? 0 : fit(B, b, q);
-            if (k == 0) {
-                b.full = true;  // no room left: the rest goes to the next batch
-                break;
+            if (k == 0 && b.nseg == 0) {  // not even one pair fits an empty batch
+                finish(S, q, PF_ENOMEM, false);
+                finished.push_back(qp);
+                queue.pop_front();
+                continue;
             }
-            place(S, b, qp, k);
-            progress = true;
-            if (q.next == q.req.n) queue.pop_front();
-            if (b.full) break;
+            if (k == 0) b.full = true;  // no room left: the rest goes to the next batch
+            else {
+                place(S, b, qp, k);
+                progress = true;
+                if (q.next == q.req.n) queue.pop_front();
+            }
+            if (b.full) {  // waits for the GPU; the next slot opens
+                B.ready.push_back(B.open);
+                B.open = -1;
+            }
         }
         place_s += std::chrono::duration<double>(clk::now() - t_place).count();
-        // launch the open batch when the GPU has no batch, or as the second
-        // one once it is large (full, or kOverlapPairs)
-        if (!S.paused.load() && B.open >= 0 && B.slots[B.open].nseg > 0 &&
+        // launch the oldest full batch, else the open one, when the GPU has
+        // no batch, or as the second one once it is large (full, or
+        // overlap_pairs)
+        int next = -1;
+        if (!B.ready.empty()) next = B.ready.front();
+        else if (B.open >= 0 && B.slots[B.open].nseg > 0) next = B.open;
+        if (!S.paused.load() && next >= 0 &&
             (B.inflight.empty() ||
              (B.inflight.size() == 1 &&
-              (B.slots[B.open].full || B.slots[B.open].pairs >= B.overlap)))) {
-            BatchSlot &b = B.slots[B.open];
+              (B.slots[next].full || B.slots[next].pairs >= B.overlap)))) {
+            if (next == B.open) B.open = -1;
+            else B.ready.pop_front();
+            BatchSlot &b = B.slots[next];
             const auto t_launch = clk::now();
+            b.t_launch = std::chrono::duration<double>(t_launch - B.t0).count();
             const pf_status st = launch(S, b);
-            launch_s += std::chrono::duration<double>(clk::now() - t_launch).count();
+            b.host_ms = std::chrono::duration<double, std::milli>(clk::now() - t_launch).count();
+            launch_s += b.host_ms * 1e-3;
             pairs_sum += (uint64_t)b.pairs;
             pairs_max = std::max(pairs_max, (uint64_t)b.pairs);
             const auto now = std::chrono::steady_clock::now();
@@ -646,8 +767,7 @@ void batch_scheduler(ServeState *Sp) {
                 S.fatal = "serve batch launch failed";
                 b.failed = true;
             }
-            B.inflight.push_back(B.open);
-            B.open = -1;
+            B.inflight.push_back(next);
             S.stats.loop_launches++;
             progress = true;
         }
@@ -683,6 +803,9 @@ void batch_stop(ServeState *Sp) {
         if (b.h_err) cudaFreeHost(b.h_err);
         if (b.ev_copied) cudaEventDestroy(b.ev_copied);
         if (b.ev_start) cudaEventDestroy(b.ev_start);
+        if (b.ev_enq) cudaEventDestroy(b.ev_enq);
+        for (auto &x : b.ev_phase)
+            if (x) cudaEventDestroy(x);
         if (b.ev_done) cudaEventDestroy(b.ev_done);
     }
     if (B.sub) pf_destroy(B.sub);
