@@ -342,6 +342,106 @@ def serve_all(pf, seconds_per_load, seed, small_batch=1 << 16):
 
 
 # ---------------------------------------------------------------------------
+# the other configurations, compact, on the default line
+
+def filter_ops(lens, E, dec):
+    """Integer operations of the method per pair, every word of every pair
+    (map 5 D W, GateKeeper 8 D W + W, SneakySnake (E+1)(3D+1), D = 2E+1,
+    W = ceil(m/32)), summed over a batch of lengths and thresholds."""
+    D = 2 * E.astype(np.int64) + 1
+    W = (lens.astype(np.int64) + 31) // 32
+    ops = 5 * D * W
+    if dec & 2:
+        ops = ops + 8 * D * W + W
+    if dec & 1:
+        ops = ops + (E.astype(np.int64) + 1) * (3 * D + 1)
+    return float(ops.sum())
+
+
+def other_configs(pf, args, rank):
+    """Configurations 1, 3 and 4 on one GPU each as a compact row: batched
+    (tuned) vs plain filter, the whole step, and the filter's fraction of the
+    integer-pipe peak.  Configurations 3 and 4 run a seeded sample of their
+    workload (4M and 2M pairs) to keep the run short."""
+    import torch
+    import synth
+    dev = torch.device("cuda", 0)
+    ctx = pf.pf_create(0)
+    peak = 152 * 64 * 2070.0 * 1e6 / 1e12
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, reps=5):
+        for _ in range(2):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / reps
+
+    out = {}
+    specs = [("cfg1_100bp_E5_100k", synth.UNIFORM, 0x5EED0000, 100_000, 100, 5, 20, 1),
+             ("cfg3_mixed_4M_sample_of_50M", synth.MIXED, 0x5EED0003, 4_000_000, 0, 0, 60, 3),
+             ("cfg4_250bp_E25_2M_sample_of_10M", synth.SKEWED_ALL, 0x5EED0004, 2_000_000, 250, 25,
+              100, 3)]
+    for name, kind, seed, n, m, e, kmax, dec in specs:
+        P = synth.generate(kind, seed + rank * 7919, n, m=m, E=e, kmax=kmax)
+        reads = torch.from_numpy(P.reads).to(dev)
+        refs = torch.from_numpy(P.refs).to(dev)
+        lens = torch.from_numpy(P.lens).to(dev)
+        E = torch.from_numpy(P.E).to(dev)
+        Emax = int(P.E.max())
+        if m:
+            W = (m + 31) // 32
+            rd = pf.Seqs.empty(n * W, dev, stride_words=W)
+            rf = pf.Seqs.empty(n * W, dev, stride_words=W)
+            pack = lambda: (pf.pf_pack_fixed(ctx, reads, n, m, rd),
+                            pf.pf_pack_fixed(ctx, refs, n, m, rf))
+        else:
+            wo, total = pf.pf_pack_layout(P.read_off)
+            bo_d = torch.from_numpy(P.read_off).to(dev)
+            wo_d = torch.from_numpy(wo).to(dev)
+            rd = pf.Seqs.empty(total, dev, word_off=wo_d)
+            rf = pf.Seqs.empty(total, dev, word_off=wo_d)
+            pack = lambda: (pf.pf_pack(ctx, reads, bo_d, wo_d, rd),
+                            pf.pf_pack(ctx, refs, bo_d, wo_d, rf))
+        pairs = pf.Pairs(rd, rf)
+        pack()
+        acc = torch.empty(2 * n, dtype=torch.uint8, device=dev)
+        cnt = torch.empty(2 * n, dtype=torch.int16, device=dev)
+        dist = torch.empty(n, dtype=torch.int32, device=dev)
+        if n >= 1 << 20:
+            pf.pf_tune_batch(ctx, 1, pairs, lens, E, Emax, n=n, sample=1 << 19, reps=1)
+            pf.pf_tune_batch(ctx, 3, pairs, lens, E, Emax, n=n, sample=1 << 19, reps=1)
+        ss_b = timed(lambda: pf.pf_filter(ctx, 1, pairs, lens, E, Emax, acc, cnt, n))
+        ss_p = timed(lambda: pf.pf_filter_plain(ctx, 1, pairs, lens, E, Emax, acc, cnt, n))
+        f_ms = timed(lambda: pf.pf_filter(ctx, dec, pairs, lens, E, Emax, acc, cnt, n))
+        if dec == 1:
+            step = lambda: (pack(), pf.pf_filter(ctx, 1, pairs, lens, E, Emax, acc, cnt, n))
+            what = "pack + SneakySnake"
+        else:
+            step = lambda: (pack(), pf.pf_filter_verify(ctx, 3, pairs, lens, E, Emax, acc, cnt,
+                                                        dist, n))
+            what = "pack + filter (both deciders) + compact + verify"
+        st_ms = timed(step)
+        row = {"pairs": n, "step": what, "step_ms": st_ms, "step_pairs_s": n / (st_ms / 1e3),
+               "sneakysnake_batched_pairs_s": n / (ss_b / 1e3),
+               "sneakysnake_plain_pairs_s": n / (ss_p / 1e3), "batched_over_plain": ss_p / ss_b,
+               "filter_ms": f_ms,
+               "filter_frac_of_alu_peak": filter_ops(P.lens, P.E, dec) / (f_ms / 1e3) / 1e12 / peak}
+        if dec == 3:
+            row["verify_all_ms"] = timed(lambda: pf.pf_verify(ctx, pairs, lens, E, Emax, None, None,
+                                                              dist, n))
+        out[name] = row
+        del reads, refs, rd, rf, pairs, acc, cnt, dist, P
+        torch.cuda.empty_cache()
+    pf.pf_destroy(ctx)
+    return out
+
+
+# ---------------------------------------------------------------------------
 # the other configurations (their own lines; the default line is the
 # 150 bp, E = 6 workload above)
 
@@ -704,6 +804,17 @@ def main_gpu(args):
     # headline comparison: SneakySnake alone, batched (tuned) vs plain kernel
     ss_batched_ms = timed(lambda: pf.pf_filter(ctx, 1, pairs, lens, E, E_HEAD, acc, cnt, n))
     ss_plain_ms = timed(lambda: pf.pf_filter_plain(ctx, 1, pairs, lens, E, E_HEAD, acc, cnt, n))
+    # where the gain comes from: the plain kernel with the threshold fixed at
+    # compile time (specialisation alone), the same fused kernel body through
+    # the scheduler's persistent launch, and the tuned two-phase form
+    ss_plain_exact_ms = timed(lambda: pf.pf_filter_plain_exact(ctx, 1, pairs, lens, E_HEAD, acc,
+                                                               cnt, n))
+    fused_cfg = [i for i, c in enumerate(pf.pf_kernel_configs())
+                 if c[3] == E_HEAD and c[4] == 0][0]
+    keep = pf.pf_tune_get(ctx, 1, E_HEAD)
+    pf.pf_tune_set(ctx, 1, E_HEAD, fused_cfg, 64)
+    ss_fused_ms = timed(lambda: pf.pf_filter(ctx, 1, pairs, lens, None, E_HEAD, acc, cnt, n))
+    pf.pf_tune_set(ctx, 1, E_HEAD, keep[0], keep[1])
 
     # The thesis's other deciders on the same batch: throughput, and accuracy
     # against the exact distances of the step (SneakySnake never rejects a
@@ -750,6 +861,7 @@ def main_gpu(args):
 
     serve = (None if args.no_serve else
              serve_all(pf, args.serve_seconds, SEED + 5 + rank, args.serve_small_batch))
+    configs = None if args.no_configs else other_configs(pf, args, rank)
 
     pk, pk_kind = peaks()
     stages = {"pack": pack_ms, "filter": filt_ms, "compact": compact_ms, "verify": verify_ms}
@@ -828,8 +940,17 @@ def main_gpu(args):
         "filter_sneakysnake": {"batched_pairs_s": n / (ss_batched_ms / 1000.0),
                                "plain_pairs_s": n / (ss_plain_ms / 1000.0),
                                "batched_over_plain": ss_plain_ms / ss_batched_ms,
-                               "tuned_cfg": list(tuned[1])},
+                               "tuned_cfg": list(tuned[1]),
+                               "split": {
+                                   "plain_runtime_E_ms": ss_plain_ms,
+                                   "plain_exact_E_ms": ss_plain_exact_ms,
+                                   "scheduler_fused_exact_E_ms": ss_fused_ms,
+                                   "scheduler_tuned_two_phase_ms": ss_batched_ms,
+                                   "specialisation": ss_plain_ms / ss_plain_exact_ms,
+                                   "persistent_launch": ss_plain_exact_ms / ss_fused_ms,
+                                   "two_phase": ss_fused_ms / ss_batched_ms}},
         "deciders": variants,
+        "configs": configs,
         "roofline": roof,
         "e2e": {"value": total / (e2e_ms / 1000.0), "unit": "pairs/s", "ms_per_step": e2e_ms,
                 "call": "pf_run_host (pinned host buffers, 1M-pair chunks, graph replay)",
@@ -898,6 +1019,8 @@ def main():
                     help="time one filter kernel instead of the step (profiling)")
     ap.add_argument("--deciders", type=int, default=3)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the compact rows of configurations 1, 3 and 4")
     ap.add_argument("--workload", default="headline",
                     choices=["headline", "cfg1", "cfg3", "cfg4", "cfg2_sweep"],
                     help="other configurations, each on its own line")

@@ -178,6 +178,14 @@ PF_API pf_status pf_filter_plain(pf_ctx *ctx, unsigned deciders, const pf_pairs 
                           const int32_t *lens, const int16_t *E, int E_max,
                           uint8_t *accept, int16_t *count, int64_t n);
 
+/* The plain kernel with one threshold E (0..15) fixed at compile time: one
+ * thread per pair, one launch, every pair filtered at E.  It separates what
+ * specialising the threshold gains from what the scheduler's batching and
+ * two-phase kernels gain.  Outputs as pf_filter; PF_EINVAL for E > 15. */
+PF_API pf_status pf_filter_plain_exact(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs,
+                                       const int32_t *lens, int E, uint8_t *accept,
+                                       int16_t *count, int64_t n);
+
 /* ---- a7: scheduler tuning --------------------------------------------------- */
 
 /* Kernel configurations of the batch scheduler.  Writes up to cap entries

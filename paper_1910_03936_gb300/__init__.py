@@ -25,7 +25,7 @@ __all__ = [
     "pf_filter_partitioned", "pf_filter_shouji", "pf_filter_shd", "PF_SHD_VACANT_ZERO",
     "PF_SHD_STREAK", "pf_set_small_batch", "pf_tune_batch", "pf_set_resolve_by_bounds",
     "pf_last_verified_count", "pf_peak_int", "PF_SERVE_BATCHED", "PF_SERVE_DEVICE_LOOP",
-    "pf_serve_trace",
+    "pf_serve_trace", "pf_filter_plain_exact",
 ]
 
 PF_SNEAKYSNAKE = 1
@@ -116,6 +116,7 @@ def load():
         "pf_pack_fixed": [P, P, I64, I, P, P, P],
         "pf_filter": [P, U, ctypes.POINTER(_Pairs), P, P, I, P, P, I64],
         "pf_filter_plain": [P, U, ctypes.POINTER(_Pairs), P, P, I, P, P, I64],
+        "pf_filter_plain_exact": [P, U, ctypes.POINTER(_Pairs), P, I, P, P, I64],
         "pf_filter_partitioned": [P, ctypes.POINTER(_Pairs), P, P, I, I, I, P, P, I64],
         "pf_filter_shouji": [P, ctypes.POINTER(_Pairs), P, P, I, P, P, I64],
         "pf_filter_shd": [P, ctypes.POINTER(_Pairs), P, P, I, U, P, P, I64],
@@ -308,6 +309,18 @@ def pf_filter(ctx, deciders, pairs, lens, E, E_max, accept, count, n=None):
 def pf_filter_plain(ctx, deciders, pairs, lens, E, E_max, accept, count, n=None):
     n = lens.numel() if n is None else n
     _filter_call(load().pf_filter_plain, ctx, deciders, pairs, lens, E, E_max, accept, count, n)
+
+
+def pf_filter_plain_exact(ctx, deciders, pairs, lens, E, accept, count, n=None):
+    """The plain kernel with one threshold E (0..15) fixed at compile time."""
+    _dt(lens, torch.int32, "lens")
+    _dt(accept, torch.uint8, "accept")
+    _dt(count, torch.int16, "count")
+    n = lens.numel() if n is None else n
+    _cur_stream(ctx)
+    cp = pairs._c()
+    _check(load().pf_filter_plain_exact(ctx.handle, int(deciders), ctypes.byref(cp), _p(lens),
+                                        int(E), _p(accept), _p(count), int(n)), ctx.handle)
 
 
 def _variant_call(fn, ctx, pairs, lens, E, E_max, extra, accept, count, n):

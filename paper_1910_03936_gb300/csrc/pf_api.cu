@@ -528,6 +528,18 @@ pf_status pf_filter_plain(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs,
                      "filter launch");
 }
 
+pf_status pf_filter_plain_exact(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs,
+                                const int32_t *lens, int E, uint8_t *accept, int16_t *count,
+                                int64_t n) {
+    pf_status st = check_filter_args(ctx, deciders, pairs, lens, E, accept, count, n);
+    if (st != PF_OK || n == 0) return st;
+    if (E > kPlainExactMaxE)
+        return ctx->fail(PF_EINVAL, "pf_filter_plain_exact: E = %d above %d", E, kPlainExactMaxE);
+    cudaSetDevice(ctx->device);
+    const FilterArgs a = make_filter_args(ctx, pairs, lens, nullptr, E, accept, count, n);
+    return ctx->cuda(launch_filter_plain_exact((int)deciders, E, a, ctx->stream), "filter launch");
+}
+
 pf_status pf_filter(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs, const int32_t *lens,
                     const int16_t *E, int E_max, uint8_t *accept, int16_t *count, int64_t n) {
     pf_status st = check_filter_args(ctx, deciders, pairs, lens, E_max, accept, count, n);

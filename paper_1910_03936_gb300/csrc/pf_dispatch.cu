@@ -12,6 +12,18 @@ const void *batched_fn_dec3(int);
 cudaError_t launch_plain_dec1(int, const FilterArgs &, cudaStream_t);
 cudaError_t launch_plain_dec2(int, const FilterArgs &, cudaStream_t);
 cudaError_t launch_plain_dec3(int, const FilterArgs &, cudaStream_t);
+cudaError_t launch_plain_exact_dec1(int, const FilterArgs &, cudaStream_t);
+cudaError_t launch_plain_exact_dec2(int, const FilterArgs &, cudaStream_t);
+cudaError_t launch_plain_exact_dec3(int, const FilterArgs &, cudaStream_t);
+
+cudaError_t launch_filter_plain_exact(int dec, int E, const FilterArgs &a, cudaStream_t st) {
+    switch (dec) {
+        case 1: return launch_plain_exact_dec1(E, a, st);
+        case 2: return launch_plain_exact_dec2(E, a, st);
+        case 3: return launch_plain_exact_dec3(E, a, st);
+    }
+    return cudaErrorInvalidValue;
+}
 
 cudaError_t launch_filter_plain(int dec, int plain_idx, const FilterArgs &a, cudaStream_t st) {
     switch (dec) {

@@ -472,6 +472,16 @@ __device__ __forceinline__ int64_t item_pairs(int64_t bin_pairs, int tuned, int 
     return c < tuned ? c : (int64_t)tuned;
 }
 
+// The plain kernel with the threshold fixed at compile time (E = XE for
+// every pair): one thread per pair, one launch, no scheduler; it isolates
+// what specialising the threshold gains over filter_plain_kernel.
+template <int XE, int DEC>
+__global__ void __launch_bounds__(256) filter_plain_exact_kernel(FilterArgs a) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.n) return;
+    filter_group<1, XE + 1, DEC, XE>(a, p, 0, 1u << (threadIdx.x & 31));
+}
+
 // The batched kernel: persistent warps take chunks of `chunk` positions of
 // one bin through an atomic counter (fewer for a short bin, item_pairs); the lane groups of a warp stride
 // through the chunk, one pair per group at a time, so neighbouring groups

@@ -78,6 +78,22 @@ static cudaError_t launch_plain_r(int i, const FilterArgs &a, cudaStream_t st) {
     return cudaErrorInvalidValue;
 }
 
+template <int XE>
+static cudaError_t launch_plain_exact_r(int E, const FilterArgs &a, cudaStream_t st) {
+    if (E == XE) {
+        const int64_t blocks = (a.n + 255) / 256;
+        filter_plain_exact_kernel<XE, PF_DEC><<<(unsigned)blocks, 256, 0, st>>>(a);
+        return cudaGetLastError();
+    }
+    if constexpr (XE + 1 <= kPlainExactMaxE) return launch_plain_exact_r<XE + 1>(E, a, st);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t PF_CAT(launch_plain_exact_dec, PF_DEC)(int E, const FilterArgs &a, cudaStream_t st) {
+    if (a.n <= 0) return cudaSuccess;
+    return launch_plain_exact_r<0>(E, a, st);
+}
+
 cudaError_t PF_CAT(launch_batched_dec, PF_DEC)(int cfg, int grid, const BatchArgs &b, int bin,
                                                cudaStream_t st) {
     return launch_batched_r<0>(cfg, grid, b, bin, st);

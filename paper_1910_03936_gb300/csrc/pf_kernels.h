@@ -72,8 +72,12 @@ constexpr int kFirstExactCfg = 20;  // kBatchCfgs[20 + E] serves exactly E
 constexpr int kPlainDpt[] = {1, 2, 4, 8, 16, 32};
 constexpr int kNumPlain = sizeof(kPlainDpt) / sizeof(kPlainDpt[0]);
 
+// The plain kernel with the threshold fixed at compile time: E = 0..15.
+constexpr int kPlainExactMaxE = 15;
+
 // dec in {1, 2, 3}
 cudaError_t launch_filter_plain(int dec, int plain_idx, const FilterArgs &a, cudaStream_t st);
+cudaError_t launch_filter_plain_exact(int dec, int E, const FilterArgs &a, cudaStream_t st);
 cudaError_t launch_filter_batched(int dec, int cfg, int grid, const BatchArgs &b, int bin,
                                   cudaStream_t st);
 const void *filter_batched_fn(int dec, int cfg);

@@ -313,6 +313,33 @@ def test_filter_uniform_E_without_array(ctx, case_data):
         assert np.array_equal(c, oc) and np.array_equal(a, oa)
 
 
+@pytest.mark.parametrize("name", ["cfg1_uniform_100bp_E5", "cfg2_150bp_E0", "cfg2_150bp_E1",
+                                  "cfg2_150bp_E6", "cfg2_150bp_E11", "cfg2_150bp_E15"])
+@pytest.mark.parametrize("dec", [1, 2, 3])
+def test_plain_exact_threshold_kernel(pf, ctx, case_data, name, dec):
+    # one compile-time threshold for every pair of the batch
+    P, D, (oa, oc) = case_data[name]
+    E = int(P.E[0])
+    slots = 2 if dec == 3 else 1
+    acc = torch.full((slots * D.n,), 0xEE, dtype=torch.uint8, device="cuda:0")
+    cnt = torch.full((slots * D.n,), -7, dtype=torch.int16, device="cuda:0")
+    pf.pf_filter_plain_exact(ctx, dec, D.pairs, D.lens, E, acc, cnt, D.n)
+    pf.pf_sync(ctx)
+    a = acc.cpu().numpy().reshape(slots, D.n)
+    c = cnt.cpu().numpy().reshape(slots, D.n)
+    want = [0, 1] if dec == 3 else [dec - 1]
+    assert np.array_equal(c, oc[want]) and np.array_equal(a, oa[want])
+
+
+def test_plain_exact_threshold_rejects_large_E(pf, ctx, case_data):
+    P, D, _ = case_data["cfg2_150bp_E6"]
+    acc = torch.zeros(D.n, dtype=torch.uint8, device="cuda:0")
+    cnt = torch.zeros(D.n, dtype=torch.int16, device="cuda:0")
+    with pytest.raises(pf.PFError) as ei:
+        pf.pf_filter_plain_exact(ctx, 1, D.pairs, D.lens, 16, acc, cnt, D.n)
+    assert ei.value.status == 1
+
+
 def test_every_batched_configuration(pf, ctx):
     """Each (lanes per pair, slots per lane) kernel, each decider set, at the
     thresholds it serves, against the oracle."""
