@@ -285,7 +285,8 @@ def serve_reference_rates(pf, ctx, seed, n=4_000_000):
 
 def serve_measure(pf, ctx, seconds_per_load, seed, mode=0, ref=None, loads=(0.25, 0.5, 0.9)):
     """Serving through pf_serve_replay.  Peak = pairs/s of a burst of every
-    request of the pool (16 times over, about 25M pairs) submitted at once; then Poisson
+    request of the pool (16 times over, about 25M pairs) submitted at once,
+    the best of three; then Poisson
     arrivals at fractions of that peak and, when it is below the peak, at a
     quarter of the batched path's device throughput (ref).  Latency = submit
     to results in host memory."""
@@ -294,9 +295,13 @@ def serve_measure(pf, ctx, seconds_per_load, seed, mode=0, ref=None, loads=(0.25
     pf.pf_serve_start(ctx, mode=mode)
     pf.pf_serve_replay(ctx, pool[:8], np.zeros(8))           # warm-up
     burst = np.zeros(16 * len(pool))
-    st, lat, el = pf.pf_serve_replay(ctx, pool, burst)
-    peak = 16 * float(sizes.sum()) / el
+    bursts = []
+    for _ in range(3):   # the host is shared: the best of three bursts
+        st, lat, el = pf.pf_serve_replay(ctx, pool, burst)
+        bursts.append(16 * float(sizes.sum()) / el)
+    peak = max(bursts)
     out = {"mode": "batched" if mode == 0 else "device_loop", "peak_pairs_s": peak,
+           "burst_pairs_s": bursts,
            "requests_pool": len(pool), "mean_request_pairs": mean_pairs, "status": int(st),
            "buffers": "page-locked host"}
     points = [("load_%d" % int(f * 100), f * peak) for f in loads]
