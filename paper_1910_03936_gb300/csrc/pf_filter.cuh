@@ -614,4 +614,107 @@ __global__ void __launch_bounds__(kSplitWarps * 32, (XE <= 7 ? 5 : (XE <= 10 ? 4
     }
 }
 
+// ---- Two-phase form with a lane group per pair (large thresholds) ----------
+//
+// For large E one thread cannot hold the 2E+1 masks of GateKeeper's three
+// words in registers.  Here TPP lanes share a pair (each owns DPT diagonal
+// slots, as in the fused group loop): the first phase builds the mask words
+// of the whole pair and runs GateKeeper, every lane storing its own slots'
+// words in its own shared-memory column; the second runs SneakySnake as a
+// per-group loop of steps over the stored words, one group AND per step.
+// The walk is split_sneakysnake's, with the group's lanes each folding their
+// own diagonals into T.
+template <int TPP, int DPT>
+__device__ __forceinline__ int split_sneakysnake_group(const uint32_t *mine, int W, int E, int g,
+                                                       unsigned gmask, uint32_t neg1) {
+    if (W == 0) return 0;
+    unsigned live = 0u;  // this lane's live slots
+#pragma unroll
+    for (int k = 0; k < DPT; ++k) {
+        const int d = slot_d<TPP, DPT, -1>(k, g);
+        if (d <= E && -d <= E) live |= 1u << k;
+    }
+    uint32_t Mw[DPT];
+#pragma unroll
+    for (int k = 0; k < DPT; ++k) Mw[k] = ((live >> k) & 1u) ? mine[k * 32] : 0u;
+    int ws = 0, kss = 0;
+    uint32_t C = 0xffffffffu;
+    for (;;) {
+        uint32_t y[DPT];
+        uint32_t T = 0xffffffffu;
+#pragma unroll
+        for (int k = 0; k < DPT; ++k) {
+            y[k] = Mw[k] & C;
+            if ((live >> k) & 1u) T &= y[k] | (y[k] * neg1);
+        }
+        T = group_and<TPP>(T, gmask);
+        const int pbit = __ffs(T) - 1;  // the obstacle passed; -1 if T == 0
+        if (T != 0u) {
+            if (++kss > E) break;
+            if (pbit != 31) {
+                C = 0xfffffffeu << pbit;
+                continue;
+            }
+        }
+        if (ws == W - 1) break;
+        ++ws;
+        const uint32_t cm = (T == 0u) ? 1u : 0u;
+#pragma unroll
+        for (int k = 0; k < DPT; ++k)
+            Mw[k] = ((live >> k) & 1u) ? (mine[(ws * DPT + k) * 32] | min(y[k], cm)) : 0u;
+        C = 0xffffffffu;
+    }
+    return kss > E + 1 ? E + 1 : kss;
+}
+
+template <int DEC, int TPP, int DPT, int WMAX>
+__device__ __forceinline__ void filter_split_group_pair(const FilterArgs &a, int64_t p, int g,
+                                                        unsigned gmask, uint32_t *mine) {
+    int m, E;
+    if (!pair_args<TPP, DPT, DEC, -1>(a, p, g, &m, &E)) return;
+    const int W = (m + 31) >> 5;
+    if (W > WMAX) {  // longer than the shared arrays: the fused loop
+        filter_group<TPP, DPT, DEC, -1>(a, p, g, gmask);
+        return;
+    }
+    PairFilter<TPP, DPT, DEC & 2, -1, LdNC, true> st;
+    st.sink = mine;
+    st.init(a.pairs, p, m, E);
+    st.run(a.pairs, g, gmask);
+    int ssc = 0, gkc = 0;
+    st.finish(g, gmask, &ssc, &gkc);
+    if constexpr (DEC & 1) ssc = split_sneakysnake_group<TPP, DPT>(mine, W, E, g, gmask, st.neg1);
+    if (g == 0) write_outputs<DEC>(a, p, E, ssc, gkc, st.h);
+}
+
+// Shared memory: kSplitWarps warps x WMAX words x DPT slots x 32 lanes.
+template <int DEC, int TPP, int DPT, int WMAX>
+__global__ void __launch_bounds__(kSplitWarps * 32)
+    filter_split_group_kernel(BatchArgs b, int bin) {
+    extern __shared__ uint32_t split_maps[];
+    const int lane = threadIdx.x & 31;
+    const int g = lane & (TPP - 1);
+    const unsigned gmask =
+        (TPP == 32) ? 0xffffffffu : (((1u << TPP) - 1u) << (lane & ~(TPP - 1)));
+    constexpr int GPW = 32 / TPP;  // groups per warp
+    const int gid = lane / TPP;
+    uint32_t *mine = split_maps + (threadIdx.x >> 5) * (WMAX * DPT * 32) + lane;
+    const int64_t lo = b.bin_start[bin], hi = b.bin_start[bin + 1];
+    const int64_t chunk = item_pairs(hi - lo, b.chunk, GPW);
+    unsigned long long *counter = b.work + bin;
+    const int64_t *order = (b.order && !(b.ident && *b.ident)) ? b.order : nullptr;
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(counter, 1ull);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        const int64_t s = lo + (int64_t)item * chunk;
+        if (s >= hi) break;
+        const int64_t e = min(hi, s + chunk);
+        for (int64_t q = s + gid; q < e; q += GPW) {
+            const int64_t p = order ? __ldg(order + q) : q;
+            filter_split_group_pair<DEC, TPP, DPT, WMAX>(b.f, p, g, gmask, mine);
+        }
+    }
+}
+
 }  // namespace pf

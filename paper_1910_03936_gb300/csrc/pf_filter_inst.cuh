@@ -21,7 +21,12 @@ template <int I>
 static const void *batched_ptr_i() {
     constexpr KernelCfg c = kBatchCfgs[I];
     if constexpr (cfg_split(c, PF_DEC)) {
-        const void *f = reinterpret_cast<const void *>(&filter_split_kernel<PF_DEC, c.xe, c.words>);
+        const void *f;
+        if constexpr (c.tpp == 1)
+            f = reinterpret_cast<const void *>(&filter_split_kernel<PF_DEC, c.xe, c.words>);
+        else
+            f = reinterpret_cast<const void *>(
+                &filter_split_group_kernel<PF_DEC, c.tpp, c.dpt, c.words>);
         static std::atomic<bool> raised[kMaxDevices];
         int dev = 0;
         cudaGetDevice(&dev);
@@ -41,8 +46,12 @@ static cudaError_t launch_batched_i(int grid, const BatchArgs &b, int bin, cudaS
     constexpr KernelCfg c = kBatchCfgs[I];
     if constexpr (cfg_split(c, PF_DEC)) {
         batched_ptr_i<I>();  // sets the shared-memory limit once
-        filter_split_kernel<PF_DEC, c.xe, c.words>
-            <<<grid, cfg_threads(c, PF_DEC), cfg_smem(c, PF_DEC), st>>>(b, bin);
+        if constexpr (c.tpp == 1)
+            filter_split_kernel<PF_DEC, c.xe, c.words>
+                <<<grid, cfg_threads(c, PF_DEC), cfg_smem(c, PF_DEC), st>>>(b, bin);
+        else
+            filter_split_group_kernel<PF_DEC, c.tpp, c.dpt, c.words>
+                <<<grid, cfg_threads(c, PF_DEC), cfg_smem(c, PF_DEC), st>>>(b, bin);
     } else {
         filter_batched_kernel<c.tpp, c.dpt, PF_DEC, c.xe><<<grid, 256, 0, st>>>(b, bin);
     }

@@ -40,26 +40,30 @@ constexpr KernelCfg kBatchCfgs[] = {
     // and for E = 11..15 (up to 79 KB per block, two or three per SM)
     {1, 12, 11, 11, 5},  {1, 13, 12, 12, 5},  {1, 14, 13, 13, 5},  {1, 15, 14, 14, 5},
     {1, 16, 15, 15, 5},
+    // two-phase forms with a lane group per pair (pairs up to 256 bases): for
+    // thresholds whose masks do not fit one thread
+    {4, 4, 7, -1, 8},    {4, 8, 15, -1, 8},   {8, 4, 15, -1, 8},   {4, 16, 31, -1, 8},
+    {8, 8, 31, -1, 8},   {16, 4, 31, -1, 8},
 };
 
 // The two-phase form applies where SneakySnake runs (deciders 1 and 3);
 // GateKeeper alone runs a two-phase configuration as the fused loop.
 constexpr bool cfg_split(const KernelCfg &c, int dec) { return c.words > 0 && dec != 2; }
+// Diagonal slots one lane stores per word in the two-phase form.
+constexpr int cfg_slots(const KernelCfg &c) { return c.xe >= 0 ? 2 * c.xe + 1 : c.dpt; }
 // Block size and dynamic shared memory of a configuration's kernel.
 constexpr int cfg_threads(const KernelCfg &c, int dec) {
     return cfg_split(c, dec) ? kSplitWarps * 32 : 256;
 }
 constexpr size_t cfg_smem(const KernelCfg &c, int dec) {
     return cfg_split(c, dec)
-               ? (size_t)kSplitWarps * c.words * (2 * c.xe + 1) * 32 * sizeof(uint32_t)
+               ? (size_t)kSplitWarps * c.words * cfg_slots(c) * 32 * sizeof(uint32_t)
                : 0;
 }
 
 // Pairs one warp of a configuration's kernel takes at once: one per lane in
 // the two-phase form, one per lane group in the fused loop.
-constexpr int cfg_step(const KernelCfg &c, int dec) {
-    return cfg_split(c, dec) ? 32 : 32 / c.tpp;
-}
+constexpr int cfg_step(const KernelCfg &c, int dec) { return 32 / c.tpp; }
 
 // a configuration serves threshold E
 constexpr bool cfg_serves(const KernelCfg &c, int E) {

@@ -583,32 +583,35 @@ def test_two_phase_configs_on_ragged_pairs(pf, ctx, case_data):
 
 
 def test_every_two_phase_config_bit_exact(pf, ctx):
-    """Every two-phase configuration, forced for its threshold, on pairs
-    that fit its shared arrays (150 bp) and on pairs that overflow them
-    (200 bp, 7 words: the fused loop in the same warps), both decider sets."""
+    """Every two-phase configuration, forced for the thresholds it serves,
+    on pairs that fit its shared arrays (150 bp; 250 bp for the lane-group
+    forms with 8-word arrays) and on pairs that overflow them (200 bp, 7
+    words; 300 bp: the fused loop in the same warps), both decider sets."""
     from gpu_util import DevicePairs, filter_dev
     cfgs = pf.pf_kernel_configs()
     data = {}
     for i, (tpp, dpt, ecap, xe, words) in enumerate(cfgs):
         if words <= 0:
             continue
-        for m in (150, 200):
-            if (xe, m) not in data:
-                P = synth.generate(synth.SKEWED, 0x5EED0C00 + 97 * xe + m, 1500, m=m, E=xe,
-                                   kmax=40)
-                data[(xe, m)] = (DevicePairs(ctx, P, fixed=m), oracle_filter(P, 3))
-            D, (oa, oc) = data[(xe, m)]
+        cases = [(xe, 150), (xe, 200)] if xe >= 0 else \
+            [(ecap, 250), (ecap, 300), (max(ecap // 2, 1), 250)]
+        for E, m in cases:
+            if (E, m) not in data:
+                P = synth.generate(synth.SKEWED, 0x5EED0C00 + 97 * E + m, 1500, m=m, E=E,
+                                   kmax=max(40, 3 * E))
+                data[(E, m)] = (DevicePairs(ctx, P, fixed=m), oracle_filter(P, 3))
+            D, (oa, oc) = data[(E, m)]
             for dec in (1, 3):
-                before = pf.pf_tune_get(ctx, dec, xe)
-                pf.pf_tune_set(ctx, dec, xe, i, 64)
+                before = pf.pf_tune_get(ctx, dec, E)
+                pf.pf_tune_set(ctx, dec, E, i, 64)
                 try:
                     a, c = filter_dev(ctx, D, dec)
                 finally:
-                    pf.pf_tune_set(ctx, dec, xe, *before)
+                    pf.pf_tune_set(ctx, dec, E, *before)
                 want_c = oc if dec == 3 else oc[[0]]
                 want_a = oa if dec == 3 else oa[[0]]
-                assert np.array_equal(c, want_c), (i, m, dec)
-                assert np.array_equal(a, want_a), (i, m, dec)
+                assert np.array_equal(c, want_c), (i, m, E, dec)
+                assert np.array_equal(a, want_a), (i, m, E, dec)
 
 
 # ---- scheduler tuning ------------------------------------------------------------
