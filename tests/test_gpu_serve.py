@@ -250,3 +250,28 @@ def test_batched_uses_the_serving_contexts_tuning(pf, ctx):
         assert pf.pf_wait(ctx, R.ticket, 60000)[0] == 0
         check(P, R, 3)
         pf.pf_serve_stop(ctx)
+
+
+def test_batched_trace_accounts_for_every_pair(pf, ctx):
+    pf.pf_serve_start(ctx, mode=0, batch_pairs=3000)
+    reqs = [make_request(pf, 600 + i, n, pinned=True) for i, n in enumerate((4000, 1500, 9000))]
+    for _, R in reqs:
+        pf.pf_submit(ctx, R)
+    for P, R in reqs:
+        assert pf.pf_wait(ctx, R.ticket, 60000)[0] == 0
+        check(P, R, 3)
+    tr = pf.pf_serve_trace(ctx)
+    total = sum(P.n for P, _ in reqs)
+    assert len(tr) >= total // 3000 and tr[:, 2].sum() == total
+    assert (tr[:, 2] <= 3000).all() and (tr[:, 3] >= 1).all()
+    assert (tr[:, 1] >= tr[:, 0]).all() and (tr[:, 5] > 0).all()
+    assert (tr[:, 8:13] >= 0).all() and (tr[:, 7] == 3).all()
+    st = pf.pf_serve_stats_get(ctx)
+    assert st["batch_pairs"] == total and st["loop_launches"] == len(tr)
+    pf.pf_serve_stop(ctx)
+    with pytest.raises(pf.PFError):
+        pf.pf_serve_trace(ctx)           # not serving
+    pf.pf_serve_start(ctx, mode=1)
+    with pytest.raises(pf.PFError):
+        pf.pf_serve_trace(ctx)           # the device loop keeps no batch trace
+    pf.pf_serve_stop(ctx)
