@@ -893,7 +893,7 @@ def main_gpu(args):
     # the kernels as captured (the two-phase exact-E6 filter with 5-word
     # arrays that the tuner picks; pack_stream, one launch per 2M sequences,
     # two per pair; verify<u32> on the pairs left after equal bounds)
-    traffic_per_pair = {"filter": (248.146432e6 + 11.001856e6) / 2e6,
+    traffic_per_pair = {"filter": (248.0896e6 + 10.408448e6) / 2e6,
                         "pack": 2 * (300.054784e6 + 91.782656e6) / 2e6,
                         "verify": (173.886208e6 + 5.08544e6) / 2e6}
     sm_mhz = clk.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
