@@ -311,15 +311,33 @@ def serve_measure(pf, ctx, seconds_per_load, seed, mode=0, ref=None, loads=(0.25
         lam = offered / mean_pairs
         count = max(50, int(lam * seconds_per_load))
         arr = np.cumsum(rng.exponential(1.0 / lam, size=count))
+        n0 = len(pf.pf_serve_trace(ctx)) if mode == 0 else 0
         st, lat, el = pf.pf_serve_replay(ctx, pool, arr)
         done_pairs = float(sum(sizes[i % len(pool)] for i in range(count)))
         out[name] = {
             "offered_pairs_s": offered, "throughput_pairs_s": done_pairs / el,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "requests": count, "status": int(st)}
+        if mode == 0:
+            out[name]["batches"] = trace_summary(pf.pf_serve_trace(ctx)[n0:])
     out["stats"] = pf.pf_serve_stats_get(ctx)
     pf.pf_serve_stop(ctx)
     return out
+
+
+def trace_summary(tr):
+    """Per-batch times of a load point (pf_serve_trace): p50 / p99 / max of
+    the batch's span (enqueue to completion seen), its wait for uploads, its
+    GPU time, and what is left of the span (queued behind the batch before
+    it, and the scheduler seeing completion)."""
+    if len(tr) == 0:
+        return None
+    span = (tr[:, 1] - tr[:, 0]) * 1e3
+    rest = span - np.maximum(tr[:, 4], 0) - tr[:, 5]
+    q = lambda a: [round(float(np.percentile(a, 50)), 3), round(float(np.percentile(a, 99)), 3),
+                   round(float(a.max()), 3)]
+    return {"count": int(len(tr)), "pairs_p50": float(np.median(tr[:, 2])), "span_ms": q(span),
+            "upload_wait_ms": q(tr[:, 4]), "gpu_ms": q(tr[:, 5]), "rest_ms": q(rest)}
 
 
 def serve_all(pf, seconds_per_load, seed, small_batch=1 << 16):
