@@ -657,6 +657,13 @@ def main_gpu(args):
 
     n = args.pairs
     p0 = shard_start(rank, n)
+    # Serving first: its latency tails depend on the host side of the
+    # page-locked uploads, which the large page-locked buffers and the host
+    # traffic of the measurements below disturb (measured: p99 at 25% load
+    # 1.1 ms first in a process, 4.5 ms after the rest of the bench).
+    serve = None
+    if args.stage == "step" and not args.no_serve and not args.no_extras:
+        serve = serve_all(pf, args.serve_seconds, SEED + 5 + rank, args.serve_small_batch)
     t_gen = time.perf_counter()
     P = synth.generate(synth.SKEWED, SEED, n, m=M, E=E_HEAD, kmax=KMAX, p0=p0)
     t_gen = time.perf_counter() - t_gen
@@ -882,8 +889,6 @@ def main_gpu(args):
     e2e_ms = max_over_ranks((time.perf_counter() - t_e) * 1000.0 / e2e_steps, dist)
     pf.pf_sync(ctx)
 
-    serve = (None if args.no_serve else
-             serve_all(pf, args.serve_seconds, SEED + 5 + rank, args.serve_small_batch))
     configs = None if args.no_configs else other_configs(pf, args, rank)
 
     pk, pk_kind = peaks()
