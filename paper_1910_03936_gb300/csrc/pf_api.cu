@@ -202,11 +202,13 @@ int pf::pf_default_cfg(int E) {
         for (int c = 0; c < kNumBatchCfgs; ++c)
             if (kBatchCfgs[c].xe == E && kBatchCfgs[c].words >= 8) return c;
     if (E <= 15) return kFirstExactCfg + E;
+    // eight lanes per pair, the fewest slots that hold the 2E+1 diagonals
+    int best = -1;
     for (int c = 0; c < kNumBatchCfgs; ++c)
         if (kBatchCfgs[c].tpp == 8 && kBatchCfgs[c].xe < 0 && kBatchCfgs[c].ecap >= E &&
-            kBatchCfgs[c].words >= 8)
-            return c;
-    return -1;
+            kBatchCfgs[c].words >= 8 && (best < 0 || kBatchCfgs[c].ecap < kBatchCfgs[best].ecap))
+            best = c;
+    return best;
 }
 
 // E = 0 compares one diagonal and is bound by memory: the plain kernel

@@ -44,6 +44,9 @@ constexpr KernelCfg kBatchCfgs[] = {
     // thresholds whose masks do not fit one thread
     {4, 4, 7, -1, 8},    {4, 8, 15, -1, 8},   {8, 4, 15, -1, 8},   {4, 16, 31, -1, 8},
     {8, 8, 31, -1, 8},   {16, 4, 31, -1, 8},
+    // fewer slots per lane, fewer dead ones: 56 slots for E <= 27, 48 for
+    // E <= 23, 40 for E <= 19
+    {8, 7, 27, -1, 8},   {8, 6, 23, -1, 8},   {8, 5, 19, -1, 8},
 };
 
 // The two-phase form applies where SneakySnake runs (deciders 1 and 3);
