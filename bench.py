@@ -422,14 +422,14 @@ def other_configs(pf, args, rank):
             rf = pf.Seqs.empty(n * W, dev, stride_words=W)
             pack = lambda: (pf.pf_pack_fixed(ctx, reads, n, m, rd),
                             pf.pf_pack_fixed(ctx, refs, n, m, rf))
-        else:
-            wo, total = pf.pf_pack_layout(P.read_off)
+        else:  # grouped by threshold and length, as the mixed workload's own line
+            ws, total = pf.pf_pack_layout_grouped(P.read_off, P.E)
             bo_d = torch.from_numpy(P.read_off).to(dev)
-            wo_d = torch.from_numpy(wo).to(dev)
-            rd = pf.Seqs.empty(total, dev, word_off=wo_d)
-            rf = pf.Seqs.empty(total, dev, word_off=wo_d)
-            pack = lambda: (pf.pf_pack(ctx, reads, bo_d, wo_d, rd),
-                            pf.pf_pack(ctx, refs, bo_d, wo_d, rf))
+            ws_d = torch.from_numpy(ws).to(dev)
+            rd = pf.Seqs.empty(total, dev, word_off=ws_d)
+            rf = pf.Seqs.empty(total, dev, word_off=ws_d)
+            pack = lambda: (pf.pf_pack_starts(ctx, reads, bo_d, ws_d, rd),
+                            pf.pf_pack_starts(ctx, refs, bo_d, ws_d, rf))
         pairs = pf.Pairs(rd, rf)
         pack()
         acc = torch.empty(2 * n, dtype=torch.uint8, device=dev)
@@ -568,12 +568,15 @@ def run_other_workload(args):
         pack = lambda: (pf.pf_pack_fixed(ctx, reads, n, fixed, rd),
                         pf.pf_pack_fixed(ctx, refs, n, fixed, rf))
     else:
-        wo, total = pf.pf_pack_layout(P.read_off)
+        # the packed layout grouped by threshold and length: the pairs each
+        # bin's launch runs lie together in the planes
+        ws, total = pf.pf_pack_layout_grouped(P.read_off, P.E)
         bo_d = torch.from_numpy(P.read_off).to(dev)
-        wo_d = torch.from_numpy(wo).to(dev)
-        rd = pf.Seqs.empty(total, dev, word_off=wo_d)
-        rf = pf.Seqs.empty(total, dev, word_off=wo_d)
-        pack = lambda: (pf.pf_pack(ctx, reads, bo_d, wo_d, rd), pf.pf_pack(ctx, refs, bo_d, wo_d, rf))
+        ws_d = torch.from_numpy(ws).to(dev)
+        rd = pf.Seqs.empty(total, dev, word_off=ws_d)
+        rf = pf.Seqs.empty(total, dev, word_off=ws_d)
+        pack = lambda: (pf.pf_pack_starts(ctx, reads, bo_d, ws_d, rd),
+                        pf.pf_pack_starts(ctx, refs, bo_d, ws_d, rf))
     pairs = pf.Pairs(rd, rf)
     pack()
     acc = torch.zeros(2 * n, dtype=torch.uint8, device=dev)

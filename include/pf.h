@@ -150,6 +150,33 @@ PF_API pf_status pf_pack(pf_ctx *ctx, const uint8_t *ascii, const int64_t *byte_
                   const int64_t *word_off, int64_t nseq,
                   uint32_t *lo, uint32_t *hi, uint32_t *nmask);
 
+/* A ragged layout grouped by threshold and length, for batches whose
+ * pairs carry their own E.  The scheduler runs the pairs of one threshold
+ * together (in pair order); laid out in pair order, they are scattered over
+ * the planes and each one's words cost whole DRAM sectors of their own.
+ * Here sequence s gets its ceil(len/32) words (len from byte_off_host) in
+ * the order of (E_host[s], min(ceil(len/32), 64), s): the pairs of one
+ * threshold and length lie back to back, in pair order.  E_host: host
+ * int16[nseq] (pair p's read and reference are sequence p of two
+ * buffers packed with the same layout), or NULL to group by length alone.
+ * Writes each sequence's first word into word_start_host (host int64[nseq],
+ * may be NULL) and the planes' size into *total_words.  PF_EINVAL if an
+ * offset falls or an E_host[s] is outside [0, PF_MAX_E]. */
+PF_API pf_status pf_pack_layout_grouped(const int64_t *byte_off_host, const int16_t *E_host,
+                                        int64_t nseq, int64_t *word_start_host,
+                                        int64_t *total_words);
+
+/* Pack nseq ASCII sequences into words given per sequence: word_start is
+ * device int64[nseq], and sequence s (bytes [byte_off[s], byte_off[s+1]))
+ * occupies words [word_start[s], word_start[s] + ceil(len/32)) of each
+ * plane, in any order; the ranges must not overlap and must lie inside
+ * the caller's planes (pf_pack_layout_grouped's do, for planes of
+ * *total_words words).  Otherwise as pf_pack.  The sequences are then
+ * addressed with word_off = word_start in pf_seqs. */
+PF_API pf_status pf_pack_starts(pf_ctx *ctx, const uint8_t *ascii, const int64_t *byte_off,
+                                const int64_t *word_start, int64_t nseq, uint32_t *lo,
+                                uint32_t *hi, uint32_t *nmask);
+
 /* Same for nseq sequences of one length len stored back to back:
  * sequence s is ascii[s*len, (s+1)*len) and occupies words
  * [s*W, (s+1)*W) with W = ceil(len/32). */

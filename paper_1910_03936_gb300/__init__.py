@@ -25,7 +25,7 @@ __all__ = [
     "pf_filter_partitioned", "pf_filter_shouji", "pf_filter_shd", "PF_SHD_VACANT_ZERO",
     "PF_SHD_STREAK", "pf_set_small_batch", "pf_tune_batch", "pf_set_resolve_by_bounds",
     "pf_last_verified_count", "pf_peak_int", "PF_SERVE_BATCHED", "PF_SERVE_DEVICE_LOOP",
-    "pf_serve_trace", "pf_filter_plain_exact",
+    "pf_serve_trace", "pf_filter_plain_exact", "pf_pack_layout_grouped", "pf_pack_starts",
 ]
 
 PF_SNEAKYSNAKE = 1
@@ -113,6 +113,8 @@ def load():
         "pf_sync": [P],
         "pf_pack_layout": [P, I64, P, ctypes.POINTER(ctypes.c_int64)],
         "pf_pack": [P, P, P, P, I64, P, P, P],
+        "pf_pack_layout_grouped": [P, P, I64, P, ctypes.POINTER(ctypes.c_int64)],
+        "pf_pack_starts": [P, P, P, P, I64, P, P, P],
         "pf_pack_fixed": [P, P, I64, I, P, P, P],
         "pf_filter": [P, U, ctypes.POINTER(_Pairs), P, P, I, P, P, I64],
         "pf_filter_plain": [P, U, ctypes.POINTER(_Pairs), P, P, I, P, P, I64],
@@ -272,6 +274,38 @@ def pf_pack_layout(byte_off):
     return wo, int(total.value)
 
 
+def pf_pack_layout_grouped(byte_off, E=None):
+    """Host int64 byte offsets (nseq+1) and optional host int16 thresholds
+    (nseq) -> (word_start numpy int64[nseq], total words)."""
+    import numpy as np
+    bo = np.ascontiguousarray(byte_off, dtype=np.int64)
+    nseq = len(bo) - 1
+    Eh = None
+    if E is not None:
+        Eh = np.ascontiguousarray(E, dtype=np.int16)
+        if Eh.shape != (nseq,):
+            raise ValueError("E must hold one threshold per sequence")
+    ws = np.zeros(max(nseq, 0), dtype=np.int64)
+    total = ctypes.c_int64()
+    _check(load().pf_pack_layout_grouped(
+        ctypes.c_void_p(bo.ctypes.data), ctypes.c_void_p(Eh.ctypes.data) if Eh is not None else None,
+        nseq, ctypes.c_void_p(ws.ctypes.data), ctypes.byref(total)))
+    return ws, int(total.value)
+
+
+def pf_pack_starts(ctx, ascii, byte_off, word_start, out):
+    """Pack ragged ASCII into ``out`` (a Seqs) at per-sequence first words."""
+    _dt(ascii, torch.uint8, "ascii")
+    _dt(byte_off, torch.int64, "byte_off")
+    _dt(word_start, torch.int64, "word_start")
+    nseq = byte_off.numel() - 1
+    if word_start.numel() < nseq:
+        raise ValueError("word_start needs one entry per sequence")
+    _cur_stream(ctx)
+    _check(load().pf_pack_starts(ctx.handle, _p(ascii), _p(byte_off), _p(word_start), nseq,
+                                 _p(out.lo), _p(out.hi), _p(out.nmask)), ctx.handle)
+
+
 def pf_pack(ctx, ascii, byte_off, word_off, out):
     """Pack ragged ASCII (uint8 device tensor) into ``out`` (a Seqs)."""
     _dt(ascii, torch.uint8, "ascii")
@@ -411,13 +445,15 @@ def pf_filter_verify(ctx, deciders, pairs, lens, E, E_max, accept, count, dist, 
            ctx.handle)
 
 
-def pack_pairs(ctx, reads, refs, length=None, byte_off=None):
+def pack_pairs(ctx, reads, refs, length=None, byte_off=None, group_E=None):
     """Pack device ASCII reads and refs (uint8 tensors) with pf_pack.
 
     Fixed length: pass ``length`` (sequence s is bytes [s*length,
     (s+1)*length)).  Ragged: pass ``byte_off`` as host int64 offsets
     (numpy, n+1 entries) shared by reads and refs; word offsets come from
-    pf_pack_layout.  Returns a :class:`Pairs`.
+    pf_pack_layout, or, with ``group_E`` (host per-pair thresholds), from
+    pf_pack_layout_grouped (packed with pf_pack_starts).  Returns a
+    :class:`Pairs`.
     """
     dev = reads.device
     if length is not None:
@@ -431,8 +467,17 @@ def pack_pairs(ctx, reads, refs, length=None, byte_off=None):
             out.append(s)
         return Pairs(out[0], out[1])
     import numpy as np
-    wo, total = pf_pack_layout(byte_off)
     bo_d = torch.from_numpy(np.ascontiguousarray(byte_off, dtype=np.int64)).to(dev)
+    if group_E is not None:
+        ws, total = pf_pack_layout_grouped(byte_off, group_E)
+        ws_d = torch.from_numpy(ws).to(dev)
+        out = []
+        for src in (reads, refs):
+            s = Seqs.empty(total, dev, word_off=ws_d)
+            pf_pack_starts(ctx, src, bo_d, ws_d, s)
+            out.append(s)
+        return Pairs(out[0], out[1])
+    wo, total = pf_pack_layout(byte_off)
     wo_d = torch.from_numpy(wo).to(dev)
     out = []
     for src in (reads, refs):

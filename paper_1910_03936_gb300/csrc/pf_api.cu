@@ -475,6 +475,54 @@ pf_status pf_pack_layout(const int64_t *byte_off_host, int64_t nseq, int64_t *wo
     return PF_OK;
 }
 
+pf_status pf_pack_layout_grouped(const int64_t *byte_off_host, const int16_t *E_host,
+                                 int64_t nseq, int64_t *word_start_host, int64_t *total_words) {
+    if (!byte_off_host || nseq < 0 || !total_words) return PF_EINVAL;
+    // classes (E, W) with W = ceil(len/32) capped at kWCap: a counting sort
+    constexpr int kWCap = 64;
+    constexpr int kW = kWCap + 1;
+    std::vector<int64_t> start((size_t)(PF_MAX_E + 1) * kW, 0);
+    auto cls = [&](int64_t s, int64_t W) {
+        const int e = E_host ? E_host[s] : 0;
+        return (size_t)e * kW + (size_t)std::min<int64_t>(W, kWCap);
+    };
+    for (int64_t s = 0; s < nseq; ++s) {
+        const int64_t len = byte_off_host[s + 1] - byte_off_host[s];
+        if (len < 0) return PF_EINVAL;
+        if (E_host && (E_host[s] < 0 || E_host[s] > PF_MAX_E)) return PF_EINVAL;
+        start[cls(s, (len + 31) / 32)] += (len + 31) / 32;
+    }
+    int64_t acc = 0;
+    for (auto &x : start) {
+        const int64_t t = x;
+        x = acc;
+        acc += t;
+    }
+    if (word_start_host)
+        for (int64_t s = 0; s < nseq; ++s) {
+            const int64_t W = (byte_off_host[s + 1] - byte_off_host[s] + 31) / 32;
+            int64_t &c = start[cls(s, W)];
+            word_start_host[s] = c;
+            c += W;
+        }
+    *total_words = acc;
+    return PF_OK;
+}
+
+pf_status pf_pack_starts(pf_ctx *ctx, const uint8_t *ascii, const int64_t *byte_off,
+                         const int64_t *word_start, int64_t nseq, uint32_t *lo, uint32_t *hi,
+                         uint32_t *nmask) {
+    if (!ctx) return PF_EINVAL;
+    if (nseq < 0) return ctx->fail(PF_EINVAL, "nseq < 0");
+    if (nseq == 0) return PF_OK;
+    if (!ascii || !byte_off || !word_start || !lo || !hi || !nmask)
+        return ctx->fail(PF_EINVAL, "null pointer argument");
+    cudaSetDevice(ctx->device);
+    return ctx->cuda(launch_pack_starts(ascii, byte_off, word_start, nseq, lo, hi, nmask,
+                                        ctx->d_err, ctx->stream),
+                     "pack launch");
+}
+
 pf_status pf_pack(pf_ctx *ctx, const uint8_t *ascii, const int64_t *byte_off,
                   const int64_t *word_off, int64_t nseq, uint32_t *lo, uint32_t *hi,
                   uint32_t *nmask) {

@@ -47,6 +47,13 @@ constexpr KernelCfg kBatchCfgs[] = {
     // fewer slots per lane, fewer dead ones: 56 slots for E <= 27, 48 for
     // E <= 23, 40 for E <= 19
     {8, 7, 27, -1, 8},   {8, 6, 23, -1, 8},   {8, 5, 19, -1, 8},
+    // one thread per pair with 8-word arrays (pairs up to 256 bases) for
+    // E = 8..13: 68 KB (three blocks per SM) to 108 KB (two) per block
+    {1, 9, 8, 8, 8},     {1, 10, 9, 9, 8},    {1, 11, 10, 10, 8},  {1, 12, 11, 11, 8},
+    {1, 13, 12, 12, 8},  {1, 14, 13, 13, 8},
+    // lane groups of two and four (fewer shuffles per step; with both
+    // deciders the fastest at E = 16..25)
+    {2, 17, 16, -1, 8},  {4, 11, 21, -1, 8},  {4, 13, 25, -1, 8},
 };
 
 // The two-phase form applies where SneakySnake runs (deciders 1 and 3);
@@ -93,6 +100,9 @@ cudaError_t launch_pack_ragged(const uint8_t *ascii, const int64_t *byte_off,
                                const int64_t *word_off, int64_t nseq, uint32_t *lo,
                                uint32_t *hi, uint32_t *nm, unsigned *err, cudaStream_t st,
                                const int32_t *seg_of = nullptr, unsigned *seg_err = nullptr);
+cudaError_t launch_pack_starts(const uint8_t *ascii, const int64_t *byte_off,
+                               const int64_t *word_start, int64_t nseq, uint32_t *lo,
+                               uint32_t *hi, uint32_t *nm, unsigned *err, cudaStream_t st);
 cudaError_t launch_pack_fixed(const uint8_t *ascii, int64_t nseq, int len, uint32_t *lo,
                               uint32_t *hi, uint32_t *nm, unsigned *err, int sms,
                               cudaStream_t st);

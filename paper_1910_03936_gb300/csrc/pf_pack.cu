@@ -78,23 +78,63 @@ __device__ __forceinline__ void decode_chunks(uintptr_t cbase, int nchunks, uint
 // with room to spare) are all N.  With seg_of given, a byte error of
 // sequence s is recorded in seg_err[seg_of[s]] instead of err (the serving
 // batches attribute errors to the request a sequence came from).
+//
+// STARTS: word_off holds each sequence's first word, in any order (a layout
+// that groups sequences by threshold and length); the block lays its
+// sequences' ceil(len/32) words out locally (a prefix sum by one warp) and
+// writes word w of sequence s to word_off[s] + w.
 constexpr int kSeqPerBlock = 128;
 
+template <bool STARTS>
 __global__ void __launch_bounds__(kPackThreads, 8)
 pack_ragged_kernel(const uint8_t *ascii, const int64_t *byte_off, const int64_t *word_off,
                    int64_t nseq, uint32_t *lo, uint32_t *hi, uint32_t *nm, unsigned *err,
                    const int32_t *seg_of, unsigned *seg_err) {
-    __shared__ int64_t woff[kSeqPerBlock + 1];
+    __shared__ int64_t woff[kSeqPerBlock + 1];  // first word of each sequence, rising
+    __shared__ int64_t wdst[STARTS ? kSeqPerBlock : 1];
     __shared__ int64_t boff[kSeqPerBlock + 1];
     __shared__ int32_t sseg[kSeqPerBlock];
     const int64_t s0 = (int64_t)blockIdx.x * kSeqPerBlock;
     const int ns = (int)min((int64_t)kSeqPerBlock, nseq - s0);
     for (int i = threadIdx.x; i <= ns; i += blockDim.x) {
-        woff[i] = word_off[s0 + i];
         boff[i] = byte_off[s0 + i];
+        if constexpr (STARTS) {
+            if (i < ns) wdst[i] = word_off[s0 + i];
+        } else {
+            woff[i] = word_off[s0 + i];
+        }
         if (seg_of && i < ns) sseg[i] = seg_of[s0 + i];
     }
     __syncthreads();
+    if constexpr (STARTS) {
+        constexpr int PER = kSeqPerBlock / 32;
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            int c[PER];
+            int sum = 0;
+#pragma unroll
+            for (int k = 0; k < PER; ++k) {
+                const int i = lane * PER + k;
+                const int64_t len = (i < ns) ? boff[i + 1] - boff[i] : 0;
+                c[k] = len > 0 ? (int)((len + 31) >> 5) : 0;
+                sum += c[k];
+            }
+            int inc = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += t;
+            }
+            int run = inc - sum;
+#pragma unroll
+            for (int k = 0; k < PER; ++k) {
+                woff[lane * PER + k] = run;
+                run += c[k];
+            }
+            if (lane == 31) woff[kSeqPerBlock] = inc;
+        }
+        __syncthreads();
+    }
     const uint8_t *lim = ascii + __ldg(byte_off + nseq);
     const int64_t base = woff[0];
     const int total = (int)(woff[ns] - base);
@@ -106,14 +146,15 @@ pack_ragged_kernel(const uint8_t *ascii, const int64_t *byte_off, const int64_t 
             if (woff[mid] <= gw) l = mid; else r = mid - 1;
         }
         const int w = (int)(gw - woff[l]);
+        const int64_t dst = STARTS ? wdst[l] + w : gw;
         const int len = (int)(boff[l + 1] - boff[l]);
         if (len - 32 * w <= 0) {
-            lo[gw] = 0u;
-            hi[gw] = 0u;
-            nm[gw] = 0xffffffffu;
+            lo[dst] = 0u;
+            hi[dst] = 0u;
+            nm[dst] = 0xffffffffu;
             continue;
         }
-        pack_word(ascii + boff[l], len, w, lo + gw, hi + gw, nm + gw,
+        pack_word(ascii + boff[l], len, w, lo + dst, hi + dst, nm + dst,
                   seg_of ? seg_err + sseg[l] : err, lim);
     }
 }
@@ -236,8 +277,18 @@ cudaError_t launch_pack_ragged(const uint8_t *ascii, const int64_t *byte_off,
                                const int32_t *seg_of, unsigned *seg_err) {
     if (nseq <= 0) return cudaSuccess;
     const int64_t blocks = (nseq + kSeqPerBlock - 1) / kSeqPerBlock;
-    pack_ragged_kernel<<<(unsigned)blocks, kPackThreads, 0, st>>>(
+    pack_ragged_kernel<false><<<(unsigned)blocks, kPackThreads, 0, st>>>(
         ascii, byte_off, word_off, nseq, lo, hi, nm, err, seg_of, seg_err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_starts(const uint8_t *ascii, const int64_t *byte_off,
+                               const int64_t *word_start, int64_t nseq, uint32_t *lo,
+                               uint32_t *hi, uint32_t *nm, unsigned *err, cudaStream_t st) {
+    if (nseq <= 0) return cudaSuccess;
+    const int64_t blocks = (nseq + kSeqPerBlock - 1) / kSeqPerBlock;
+    pack_ragged_kernel<true><<<(unsigned)blocks, kPackThreads, 0, st>>>(
+        ascii, byte_off, word_start, nseq, lo, hi, nm, err, nullptr, nullptr);
     return cudaGetLastError();
 }
 

@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import pytest
+
 from conftest import ROOT
 
 
@@ -57,3 +59,37 @@ def test_product_path_never_imports_oracle():
                 with open(os.path.join(dirpath, fn)) as f:
                     src = f.read()
                 assert "oracle" not in src.replace("oracle-free", ""), fn
+
+
+def test_grouped_layout_host_helper():
+    """pf_pack_layout_grouped: every sequence gets its ceil(len/32) words,
+    the ranges tile [0, total) without overlap, and sequences follow each
+    other in the order of (E, min(ceil(len/32), 64), index)."""
+    import numpy as np
+    import paper_1910_03936_gb300 as pf
+    rng = np.random.default_rng(3)
+    n = 5000
+    lens = rng.choice([0, 1, 31, 32, 33, 100, 150, 250, 2100, 4000], size=n)
+    E = rng.integers(0, pf.PF_MAX_E + 1, size=n).astype(np.int16)
+    bo = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(lens, out=bo[1:])
+    W = (lens + 31) // 32
+    for Eh in (E, None):
+        ws, total = pf.pf_pack_layout_grouped(bo, Eh)
+        assert total == W.sum()
+        key_e = Eh.astype(np.int64) if Eh is not None else np.zeros(n, dtype=np.int64)
+        order = np.lexsort((np.arange(n), np.minimum(W, 64), key_e))
+        expect = np.zeros(n, dtype=np.int64)
+        expect[order] = np.concatenate(([0], np.cumsum(W[order])[:-1]))
+        assert np.array_equal(ws, expect)
+    # empty batch, falling offsets, thresholds out of range
+    ws, total = pf.pf_pack_layout_grouped(np.zeros(1, dtype=np.int64), np.zeros(0, dtype=np.int16))
+    assert total == 0 and ws.size == 0
+    with pytest.raises(pf.PFError):
+        pf.pf_pack_layout_grouped(np.array([0, 5, 3], dtype=np.int64))
+    with pytest.raises(pf.PFError):
+        pf.pf_pack_layout_grouped(np.array([0, 5, 9], dtype=np.int64),
+                                  np.array([0, pf.PF_MAX_E + 1], dtype=np.int16))
+    with pytest.raises(pf.PFError):
+        pf.pf_pack_layout_grouped(np.array([0, 5, 9], dtype=np.int64),
+                                  np.array([-1, 0], dtype=np.int16))

@@ -226,6 +226,89 @@ def test_pack_ragged_blocks_and_spare_words(pf, ctx, maxlen):
                 assert got[2][g + b - a] == 0xFFFFFFFF
 
 
+@pytest.mark.parametrize("maxlen", [70, 600, 5000])
+def test_pack_starts_grouped_layout(pf, ctx, maxlen):
+    """pf_pack_starts with pf_pack_layout_grouped's word starts writes every
+    sequence's words (as the oracle packs them) where its start says, for
+    empty, short and long sequences from an unaligned start, and reports
+    bytes that are not bases inside a sequence."""
+    from gpu_util import to_dev
+    rng = np.random.default_rng(maxlen + 1)
+    n = 900
+    lens = rng.integers(0, maxlen + 1, size=n)
+    lens[rng.choice(n, 25, replace=False)] = 0
+    E = rng.integers(0, pf.PF_MAX_E + 1, size=n).astype(np.int16)
+    pre = 7
+    body = rng.choice(np.frombuffer(b"ACGTNacgtn", np.uint8), size=int(lens.sum()))
+    whole = np.concatenate([np.frombuffer(b"@" * pre, np.uint8), body,
+                            np.frombuffer(b"%" * 9, np.uint8)])
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    ws, total = pf.pf_pack_layout_grouped(off, E)
+    for bad in (False, True):
+        src = whole.copy()
+        if bad:
+            src[pre + rng.choice(len(body), 3, replace=False)] = np.frombuffer(b"#-*", np.uint8)
+        out = pf.Seqs.empty(total, "cuda:0", word_off=to_dev(ws))
+        for t in (out.lo, out.hi, out.nmask):
+            t.fill_(0x5A5A5A5A)
+        pf.pf_pack_starts(ctx, to_dev(src)[1:], to_dev(off + pre - 1), to_dev(ws), out)
+        if bad:
+            with pytest.raises(pf.PFError) as ei:
+                pf.pf_sync(ctx)
+            assert ei.value.status == 7
+        else:
+            pf.pf_sync(ctx)
+        owo, lo, hi, nm, nbad = oracle.pack_batch(src[pre:pre + len(body)], off)
+        assert nbad == (3 if bad else 0)
+        got = [t.cpu().numpy()[:total].view(np.uint32) for t in (out.lo, out.hi, out.nmask)]
+        for s_ in range(n):
+            a, b = int(owo[s_]), int(owo[s_ + 1])
+            g = int(ws[s_])
+            for plane, want in zip(got, (lo, hi, nm)):
+                assert np.array_equal(plane[g:g + b - a], want[a:b]), (maxlen, s_)
+    # the planes are covered exactly: no word left at the fill value
+    assert not np.any(got[2] == 0x5A5A5A5A)
+
+
+@pytest.mark.parametrize("dec", [1, 2, 3])
+def test_grouped_layout_whole_path_bit_exact(pf, ctx, case_data, dec):
+    """The mixed batch packed in the layout grouped by threshold and length:
+    filter and whole path equal the oracle, through the scheduler (every
+    configuration the tuner finds on it) and the plain kernel."""
+    from gpu_util import to_dev
+    P, _, (oa, oc) = case_data["cfg3_mixed"]
+    n = P.n
+    pairs = pf.pack_pairs(ctx, to_dev(P.reads), to_dev(P.refs), byte_off=P.read_off,
+                          group_E=P.E)
+    lens, E, Emax = to_dev(P.lens.astype(np.int32)), to_dev(P.E), int(P.E.max())
+    slots = 2 if dec == 3 else 1
+    want_a = oa if dec == 3 else oa[[dec - 1]]
+    want_c = oc if dec == 3 else oc[[dec - 1]]
+    before = {e: pf.pf_tune_get(ctx, dec, e) for e in range(Emax + 1)}
+    try:
+        pf.pf_tune_batch(ctx, dec, pairs, lens, E, Emax, n=n, sample=4096, reps=1)
+        for fn in (pf.pf_filter, pf.pf_filter_plain):
+            acc = torch.zeros(slots * n, dtype=torch.uint8, device="cuda:0")
+            cnt = torch.zeros(slots * n, dtype=torch.int16, device="cuda:0")
+            fn(ctx, dec, pairs, lens, E, Emax, acc, cnt, n)
+            pf.pf_sync(ctx)
+            assert np.array_equal(cnt.cpu().numpy().reshape(slots, n), want_c)
+            assert np.array_equal(acc.cpu().numpy().reshape(slots, n), want_a)
+        dist = torch.full((n,), -5, dtype=torch.int32, device="cuda:0")
+        acc = torch.zeros(slots * n, dtype=torch.uint8, device="cuda:0")
+        cnt = torch.zeros(slots * n, dtype=torch.int16, device="cuda:0")
+        pf.pf_filter_verify(ctx, dec, pairs, lens, E, Emax, acc, cnt, dist, n)
+        pf.pf_sync(ctx)
+        first = 0 if dec & 1 else 1  # the first selected decider's accepts are verified
+        vb = oracle.verify_batch(P)
+        want = np.where(oa[first] == 1, vb, P.E.astype(np.int32) + 1)
+        assert np.array_equal(dist.cpu().numpy(), want)
+        assert np.array_equal(acc.cpu().numpy().reshape(slots, n), want_a)
+    finally:
+        for e, (c, k) in before.items():
+            pf.pf_tune_set(ctx, dec, e, c, k)
+
+
 @pytest.mark.parametrize("length,n", [(1, 5000), (2, 3001), (32, 2047), (150, 4000),
                                       (4000, 300), (131072, 3), (131073, 2)])
 def test_pack_fixed_across_tiles(pf, ctx, length, n):
@@ -584,17 +667,19 @@ def test_two_phase_configs_on_ragged_pairs(pf, ctx, case_data):
 
 def test_every_two_phase_config_bit_exact(pf, ctx):
     """Every two-phase configuration, forced for the thresholds it serves,
-    on pairs that fit its shared arrays (150 bp; 250 bp for the lane-group
-    forms with 8-word arrays) and on pairs that overflow them (200 bp, 7
-    words; 300 bp: the fused loop in the same warps), both decider sets."""
+    on pairs that fit its shared arrays (150 bp; 250 bp for the forms with
+    8-word arrays) and on pairs that overflow them (200 bp, 7 words; 300 bp:
+    the fused loop in the same warps), both decider sets."""
     from gpu_util import DevicePairs, filter_dev
     cfgs = pf.pf_kernel_configs()
     data = {}
     for i, (tpp, dpt, ecap, xe, words) in enumerate(cfgs):
         if words <= 0:
             continue
-        cases = [(xe, 150), (xe, 200)] if xe >= 0 else \
-            [(ecap, 250), (ecap, 300), (max(ecap // 2, 1), 250)]
+        if xe >= 0:
+            cases = [(xe, 150), (xe, 200)] + ([(xe, 250), (xe, 300)] if words >= 8 else [])
+        else:
+            cases = [(ecap, 250), (ecap, 300), (max(ecap // 2, 1), 250)]
         for E, m in cases:
             if (E, m) not in data:
                 P = synth.generate(synth.SKEWED, 0x5EED0C00 + 97 * E + m, 1500, m=m, E=E,
