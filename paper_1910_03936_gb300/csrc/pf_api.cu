@@ -26,72 +26,151 @@ __global__ void bin_init_kernel(int64_t *bin_start, unsigned long long *work,
                                 unsigned long long *hist, int nb, int single_cfg, int64_t n) {
     for (int i = threadIdx.x; i <= nb; i += blockDim.x) {
         bin_start[i] = (single_cfg >= 0) ? (i <= single_cfg ? 0 : n) : 0;
-        if (i < nb) {
-            work[i] = 0ull;
-            hist[i] = 0ull;
-        }
+        if (i < nb) work[i] = 0ull;
     }
+    for (int i = threadIdx.x; i < kNumBinKeys; i += blockDim.x) hist[i] = 0ull;
 }
 
-__device__ __forceinline__ int bin_key(const int16_t *E, int64_t p, int E_max, const BinTable &t) {
-    int e = __ldg(E + p);
-    e = e < 0 ? 0 : (e > E_max ? E_max : e);
-    return t.cfg_of_E[e];
+// Key of pair p: its threshold's configuration, then its length class.
+// Inside a configuration the pairs of one length run together (a warp does
+// not wait on its longest pair), and in a layout grouped by threshold and
+// length (pf_pack_layout_grouped) they lie together in the planes.
+__device__ __forceinline__ int len_class(int len) {
+    const int wc = len <= 0 ? 0 : ((len - 1) >> 5) + 1;
+    return wc < kLenClasses - 1 ? wc : kLenClasses - 1;
 }
+
+// tab[e] = the first key of E = e's configuration, staged in shared memory
+// by each block (indexing the kernel parameter by a run-time threshold
+// costs far more).
+__device__ __forceinline__ void stage_keys(const BinTable &t, int *tab) {
+    if (threadIdx.x <= PF_MAX_E) tab[threadIdx.x] = t.cfg_of_E[threadIdx.x] * kLenClasses;
+}
+
+__device__ __forceinline__ int key_of(int e, int len, int E_max, const int *tab) {
+    e = e < 0 ? 0 : (e > E_max ? E_max : e);
+    return tab[e] + len_class(len);
+}
+
+// Each thread counts 8 consecutive pairs per round (one 16-byte load of
+// thresholds, two of lengths), adding a run of equal keys to its counter
+// at once.  The threshold -> key table is staged in shared memory.
+constexpr int kHistPer = 8;
 
 __global__ void __launch_bounds__(256)
-bin_hist_kernel(const int16_t *E, int64_t n, int E_max, BinTable t, unsigned long long *hist) {
-    __shared__ unsigned cnt[kNumBatchCfgs];
-    for (int i = threadIdx.x; i < kNumBatchCfgs; i += blockDim.x) cnt[i] = 0;
+bin_hist_kernel(const int16_t *E, const int32_t *lens, int64_t n, int E_max, BinTable t,
+                unsigned long long *hist) {
+    __shared__ unsigned cnt[kNumBinKeys];
+    __shared__ int tab[PF_MAX_E + 1];
+    for (int i = threadIdx.x; i < kNumBinKeys; i += blockDim.x) cnt[i] = 0;
+    stage_keys(t, tab);
     __syncthreads();
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
-         p += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(&cnt[bin_key(E, p, E_max, t)], 1u);
+    const bool vec = ((reinterpret_cast<uintptr_t>(E) | reinterpret_cast<uintptr_t>(lens)) & 15u) == 0;
+    int cur = -1;
+    unsigned run = 0;
+    auto add = [&](int e, int len) {
+        const int key = key_of(e, len, E_max, tab);
+        if (key != cur) {
+            if (run) atomicAdd(&cnt[cur], run);
+            cur = key;
+            run = 0;
+        }
+        ++run;
+    };
+    for (int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kHistPer; p0 < n;
+         p0 += (int64_t)gridDim.x * blockDim.x * kHistPer) {
+        if (vec && p0 + kHistPer <= n) {
+            const int4 ev = __ldg(reinterpret_cast<const int4 *>(E + p0));
+            const int4 la = __ldg(reinterpret_cast<const int4 *>(lens + p0));
+            const int4 lb = __ldg(reinterpret_cast<const int4 *>(lens + p0 + 4));
+            add((int16_t)(ev.x & 0xffff), la.x);
+            add((int16_t)((unsigned)ev.x >> 16), la.y);
+            add((int16_t)(ev.y & 0xffff), la.z);
+            add((int16_t)((unsigned)ev.y >> 16), la.w);
+            add((int16_t)(ev.z & 0xffff), lb.x);
+            add((int16_t)((unsigned)ev.z >> 16), lb.y);
+            add((int16_t)(ev.w & 0xffff), lb.z);
+            add((int16_t)((unsigned)ev.w >> 16), lb.w);
+        } else {
+            for (int64_t p = p0; p < n && p < p0 + kHistPer; ++p) add(__ldg(E + p), __ldg(lens + p));
+        }
+    }
+    if (run) atomicAdd(&cnt[cur], run);
     __syncthreads();
-    for (int i = threadIdx.x; i < kNumBatchCfgs; i += blockDim.x)
+    for (int i = threadIdx.x; i < kNumBinKeys; i += blockDim.x)
         if (cnt[i]) atomicAdd(&hist[i], (unsigned long long)cnt[i]);
 }
 
-// Exclusive scan of the bin sizes.  When every pair falls in one bin the
-// grouping is the identity: `ident` tells the scatter to skip and the
-// filter to index pairs directly.
+// One warp: exclusive scan of the key counts into the scatter's cursors; a
+// configuration's bin starts at its first key.  When every pair falls in
+// one configuration the grouping is the identity: `ident` tells the
+// scatter to skip and the filter to index pairs directly (pair order is
+// kept; the length classes are not separated).
 __global__ void bin_scan_kernel(const unsigned long long *hist, int64_t *bin_start,
                                 unsigned long long *cursor, int *ident) {
-    if (threadIdx.x != 0) return;
-    int64_t acc = 0;
-    int used = 0;
-    for (int i = 0; i < kNumBatchCfgs; ++i) {
-        bin_start[i] = acc;
-        cursor[i] = (unsigned long long)acc;
-        acc += (int64_t)hist[i];
-        used += hist[i] ? 1 : 0;
+    constexpr int kPer = (kNumBinKeys + 31) / 32;
+    __shared__ unsigned long long h[kNumBinKeys];
+    const int lane = threadIdx.x;
+    if (lane >= 32) return;
+    for (int i = lane; i < kNumBinKeys; i += 32) h[i] = hist[i];  // independent loads
+    __syncwarp();
+    int64_t sum = 0;
+    for (int k = 0; k < kPer; ++k) {
+        const int i = lane * kPer + k;
+        if (i < kNumBinKeys) sum += (int64_t)h[i];
     }
-    bin_start[kNumBatchCfgs] = acc;
-    *ident = (used <= 1);
+    int64_t inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    int64_t run = inc - sum;
+    for (int k = 0; k < kPer; ++k) {
+        const int i = lane * kPer + k;
+        if (i >= kNumBinKeys) break;
+        cursor[i] = (unsigned long long)run;
+        if (i % kLenClasses == 0) bin_start[i / kLenClasses] = run;
+        run += (int64_t)h[i];
+    }
+    if (lane == 31) bin_start[kNumBatchCfgs] = inc;
+    int used = 0;
+    for (int c0 = 0; c0 < kNumBatchCfgs; c0 += 32) {
+        const int c = c0 + lane;
+        bool any = false;
+        if (c < kNumBatchCfgs)
+            for (int j = 0; j < kLenClasses; ++j) any |= h[c * kLenClasses + j] != 0ull;
+        used += __popc(__ballot_sync(0xffffffffu, any));
+    }
+    if (lane == 0) *ident = (used <= 1);
 }
 
-// Each block claims room for its pairs per bin with one atomic per bin and
+// Each block claims room for its pairs per key with one atomic per key and
 // places its pairs there (order inside a block's share is arbitrary; every
 // pair keeps its own index, so results do not depend on it).
 __global__ void __launch_bounds__(256)
-bin_scatter_kernel(const int16_t *E, int64_t n, int E_max, BinTable t,
+bin_scatter_kernel(const int16_t *E, const int32_t *lens, int64_t n, int E_max, BinTable t,
                    unsigned long long *cursor, int64_t *order, const int *ident) {
-    __shared__ unsigned cnt[kNumBatchCfgs];
-    __shared__ unsigned long long base[kNumBatchCfgs];
+    __shared__ unsigned cnt[kNumBinKeys];
+    __shared__ unsigned long long base[kNumBinKeys];
+    __shared__ int tab[PF_MAX_E + 1];
     if (*ident) return;
+    stage_keys(t, tab);
     for (int64_t p0 = (int64_t)blockIdx.x * blockDim.x; p0 < n;
          p0 += (int64_t)gridDim.x * blockDim.x) {
         const int64_t p = p0 + threadIdx.x;
-        for (int i = threadIdx.x; i < kNumBatchCfgs; i += blockDim.x) cnt[i] = 0;
+        for (int i = threadIdx.x; i < kNumBinKeys; i += blockDim.x) cnt[i] = 0;
+        __syncthreads();  // tab staged; cnt zeroed
+        const int lane = threadIdx.x & 31;
+        const int key = p < n ? key_of(__ldg(E + p), __ldg(lens + p), E_max, tab) : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        const int leader = __ffs(peers) - 1;
+        unsigned r0 = 0;
+        if (key >= 0 && lane == leader) r0 = atomicAdd(&cnt[key], (unsigned)__popc(peers));
+        const unsigned rank =
+            __shfl_sync(0xffffffffu, r0, leader) + __popc(peers & ((1u << lane) - 1u));
         __syncthreads();
-        int key = -1;
-        unsigned rank = 0;
-        if (p < n) {
-            key = bin_key(E, p, E_max, t);
-            rank = atomicAdd(&cnt[key], 1u);
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < kNumBatchCfgs; i += blockDim.x)
+        for (int i = threadIdx.x; i < kNumBinKeys; i += blockDim.x)
             base[i] = cnt[i] ? atomicAdd(&cursor[i], (unsigned long long)cnt[i]) : 0ull;
         __syncthreads();
         if (p < n) order[base[key] + rank] = p;
@@ -158,9 +237,9 @@ pf_status pf_ctx::scratch_layout(int64_t n, Scratch *s) {
     const size_t o_idx = off;   off += up(nn * sizeof(int64_t));
     const size_t o_tiles = off; off += up((size_t)compact_tiles((int64_t)nn) * sizeof(int64_t));
     const size_t o_bins = off;  off += up((kNumBatchCfgs + 1) * sizeof(int64_t));
-    const size_t o_work = off;  off += up(kNumBatchCfgs * sizeof(unsigned long long));
-    const size_t o_hist = off;  off += up(kNumBatchCfgs * sizeof(unsigned long long));
-    const size_t o_cur = off;   off += up(kNumBatchCfgs * sizeof(unsigned long long));
+    const size_t o_work = off;  off += up(kWorkCounters * sizeof(unsigned long long));
+    const size_t o_hist = off;  off += up(kNumBinKeys * sizeof(unsigned long long));
+    const size_t o_cur = off;   off += up(kNumBinKeys * sizeof(unsigned long long));
     const size_t o_ident = off; off += up(sizeof(int));
     const size_t o_need = off;  off += up(nn);
     pf_status st = ensure_scratch(off);
@@ -297,17 +376,20 @@ pf_status pf_ctx::run_batched(unsigned dec, const FilterArgs &a, const Scratch &
         }
     }
     b.ident = (single < 0) ? s.ident : nullptr;
+    binned = single < 0;
     bin_init_kernel<<<1, 32, 0, stream>>>(s.bin_start, s.work, s.hist, kNumBatchCfgs, single,
                                           a.n);
     if (single < 0) {
         BinTable t;
         for (int e = 0; e <= PF_MAX_E; ++e) t.cfg_of_E[e] = tune_cfg[dec][std::min(e, a.E_max)];
         int64_t hb = std::min<int64_t>((a.n + 255) / 256, (int64_t)sms * 8);
-        bin_hist_kernel<<<(unsigned)std::max<int64_t>(hb, 1), 256, 0, stream>>>(a.E, a.n, a.E_max,
-                                                                               t, s.hist);
+        const int64_t hh = std::min<int64_t>((a.n + 256 * kHistPer - 1) / (256 * kHistPer),
+                                             (int64_t)sms * 8);
+        bin_hist_kernel<<<(unsigned)std::max<int64_t>(hh, 1), 256, 0, stream>>>(
+            a.E, a.lens, a.n, a.E_max, t, s.hist);
         bin_scan_kernel<<<1, 32, 0, stream>>>(s.hist, s.bin_start, s.cursor, s.ident);
         bin_scatter_kernel<<<(unsigned)std::max<int64_t>(hb, 1), 256, 0, stream>>>(
-            a.E, a.n, a.E_max, t, s.cursor, s.order, s.ident);
+            a.E, a.lens, a.n, a.E_max, t, s.cursor, s.order, s.ident);
     }
     pf_status st = cuda(cudaGetLastError(), "binning launch");
     if (st != PF_OK) return st;
@@ -560,6 +642,7 @@ pf_status pf_ctx::run_filter(unsigned dec, const FilterArgs &a, const Scratch &s
     // small batches: fixed costs of binning and per-bin launches dominate;
     // otherwise the plain kernel where pf_tune found it fastest for every
     // threshold the batch can hold
+    binned = false;
     bool plain = a.n < small_batch;
     if (!plain) {
         plain = true;
@@ -659,12 +742,13 @@ pf_status pf_filter_verify(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs
     if (st != PF_OK) return st;
     // the first selected decider's accept flags (less the resolved pairs)
     // choose the pairs to verify
+    // (in the scheduler's grouping, when it grouped them)
     st = ctx->cuda(launch_compact(a.need ? a.need : accept, n, s.idx, s.n_idx, s.tiles,
-                                  ctx->stream),
+                                  ctx->stream, ctx->binned ? s.order : nullptr, s.ident),
                    "compact launch");
     if (st != PF_OK) return st;
     st = ctx->cuda(launch_verify(to_view(pairs), lens, E, E_max, s.idx, s.n_idx, n, dist,
-                                 ctx->d_err, ctx->sms, ctx->stream),
+                                 ctx->d_err, ctx->sms, ctx->stream, s.work + kNumBatchCfgs),
                    "verify launch");
     ctx->verified_state = (st == PF_OK) ? 1 : 0;
     return st;
@@ -721,26 +805,42 @@ pf_status pf_tune_batch(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs,
     for (int e = 0; e <= PF_MAX_E; ++e) t.cfg_of_E[e] = e;
     const int64_t hb = std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)ctx->sms * 8));
     bin_init_kernel<<<1, 32, 0, ctx->stream>>>(s.bin_start, s.work, s.hist, kNumBatchCfgs, -1, n);
-    bin_hist_kernel<<<(unsigned)hb, 256, 0, ctx->stream>>>(E, n, E_max, t, s.hist);
+    const int64_t hh = std::max<int64_t>(
+        1, std::min<int64_t>((n + 256 * kHistPer - 1) / (256 * kHistPer), (int64_t)ctx->sms * 8));
+    bin_hist_kernel<<<(unsigned)hh, 256, 0, ctx->stream>>>(E, lens, n, E_max, t, s.hist);
     bin_scan_kernel<<<1, 32, 0, ctx->stream>>>(s.hist, s.bin_start, s.cursor, s.ident);
-    bin_scatter_kernel<<<(unsigned)hb, 256, 0, ctx->stream>>>(E, n, E_max, t, s.cursor, s.order,
-                                                               s.ident);
+    bin_scatter_kernel<<<(unsigned)hb, 256, 0, ctx->stream>>>(E, lens, n, E_max, t, s.cursor,
+                                                               s.order, s.ident);
     int64_t starts[PF_MAX_E + 2];
+    std::vector<unsigned long long> keys(kNumBinKeys);
+    int ident = 0;
     st = ctx->cuda(cudaMemcpyAsync(starts, s.bin_start, sizeof(starts), cudaMemcpyDeviceToHost,
                                    ctx->stream),
                    "pf_tune_batch bins");
+    if (st == PF_OK)
+        st = ctx->cuda(cudaMemcpyAsync(keys.data(), s.hist, kNumBinKeys * sizeof(keys[0]),
+                                       cudaMemcpyDeviceToHost, ctx->stream),
+                       "pf_tune_batch bins");
+    if (st == PF_OK)
+        st = ctx->cuda(cudaMemcpyAsync(&ident, s.ident, sizeof(int), cudaMemcpyDeviceToHost,
+                                       ctx->stream),
+                       "pf_tune_batch bins");
     if (st == PF_OK) st = ctx->cuda(cudaStreamSynchronize(ctx->stream), "pf_tune_batch sync");
     if (st != PF_OK) return st;
     const int slots = (deciders == 3u) ? 2 : 1;
     uint8_t *acc = nullptr;
     int16_t *cnt = nullptr;
     int64_t *range = nullptr;  // [2] positions timed, then the work counter
+    int64_t *sample_order = nullptr;
     if (cudaMalloc(&acc, (size_t)slots * n) != cudaSuccess ||
         cudaMalloc(&cnt, (size_t)slots * n * sizeof(int16_t)) != cudaSuccess ||
-        cudaMalloc(&range, 4 * sizeof(int64_t)) != cudaSuccess) {
+        cudaMalloc(&range, 4 * sizeof(int64_t)) != cudaSuccess ||
+        cudaMalloc(&sample_order, (size_t)std::min<int64_t>(sample, n) * sizeof(int64_t)) !=
+            cudaSuccess) {
         cudaGetLastError();
         if (acc) cudaFree(acc);
         if (cnt) cudaFree(cnt);
+        if (range) cudaFree(range);
         return ctx->fail(PF_ENOMEM, "pf_tune_batch: buffers");
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -748,19 +848,47 @@ pf_status pf_tune_batch(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs,
     cudaEventCreate(&e1);
     static const int chunks[] = {64, 256, 1024};
     for (int e = 0; e <= E_max && st == PF_OK; ++e) {
-        const int64_t lo = starts[e], hi = std::min(starts[e + 1], starts[e] + sample);
-        if (hi - lo < 1024) continue;  // too few pairs at this threshold to time
-        int64_t r[2] = {lo, hi};
-        cudaMemcpy(range, r, sizeof(r), cudaMemcpyHostToDevice);
+        const int64_t bin = starts[e + 1] - starts[e];
+        const int64_t m = std::min(bin, sample);
+        if (m < 1024) continue;  // too few pairs at this threshold to time
+        // The sample: the same share of each length class of the threshold,
+        // each share a contiguous run of the class (the pairs a launch takes
+        // together), so that the configurations are timed on the batch's
+        // mix of lengths.
+        int64_t r[2] = {0, m};
+        const int64_t *ord = s.order;
+        if (ident) {  // one threshold: pair order
+            r[0] = starts[e];
+            r[1] = starts[e] + m;
+        } else {
+            int64_t at = 0, k0 = starts[e];
+            for (int j = 0; j < kLenClasses && st == PF_OK; ++j) {
+                const int64_t cls = (int64_t)keys[e * kLenClasses + j];
+                int64_t take = (j == kLenClasses - 1) ? m - at : (cls * m) / bin;
+                take = std::min(take, cls);
+                if (take > 0)
+                    st = ctx->cuda(cudaMemcpyAsync(sample_order + at, s.order + k0,
+                                                   take * sizeof(int64_t),
+                                                   cudaMemcpyDeviceToDevice, ctx->stream),
+                                   "pf_tune_batch sample");
+                at += take;
+                k0 += cls;
+            }
+            r[1] = at;
+            ord = sample_order;
+        }
+        if (st != PF_OK) break;
+        cudaMemcpyAsync(range, r, sizeof(r), cudaMemcpyHostToDevice, ctx->stream);
+        cudaStreamSynchronize(ctx->stream);
         BatchArgs b;
         b.f = make_filter_args(ctx, pairs, lens, E, E_max, acc, cnt, n);
-        b.order = s.order;
+        b.order = ident ? nullptr : ord;
         b.bin_start = range;
         b.bin_cfg = nullptr;
         b.nbins = 1;
         b.work = reinterpret_cast<unsigned long long *>(range + 2);
         b.chunk_start = nullptr;
-        b.ident = s.ident;
+        b.ident = nullptr;
         int bc = ctx->tune_cfg[deciders][e], bk = ctx->tune_chunk[deciders][e];
         float bms = 1e30f;
         for (int c = 0; st == PF_OK && c < kNumBatchCfgs; ++c) {
@@ -769,7 +897,7 @@ pf_status pf_tune_batch(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs,
                 b.chunk = k;
                 const int wpb = cfg_threads(kBatchCfgs[c], (int)deciders) / 32;
                 const int step = cfg_step(kBatchCfgs[c], (int)deciders);
-                const int64_t steps = (hi - lo + step - 1) / step;
+                const int64_t steps = (r[1] - r[0] + step - 1) / step;
                 const int grid = (int)std::min<int64_t>(ctx->grid_for((int)deciders, c),
                                                         std::max<int64_t>(1, (steps + wpb - 1) / wpb));
                 float best = 1e30f;
@@ -802,6 +930,7 @@ pf_status pf_tune_batch(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs,
     cudaFree(acc);
     cudaFree(cnt);
     cudaFree(range);
+    cudaFree(sample_order);
     return st;
 }
 

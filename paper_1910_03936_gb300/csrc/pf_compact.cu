@@ -6,6 +6,10 @@
 //           total,
 //   scatter block b re-reads its tile and writes the positions of the set
 //           flags, in order, from its offset on.
+// With an order array (the scheduler's grouping of the pairs by
+// configuration and length) position q stands for pair order[q]: the
+// indices come out in that order, so that verification runs the pairs of
+// one threshold and length together.
 #include "pf_internal.cuh"
 
 namespace pf {
@@ -36,6 +40,21 @@ __device__ __forceinline__ unsigned load_flags16(const uint8_t *flags, int64_t b
     return bits;
 }
 
+// The same through an order array: position q's flag is flags[order[q]].
+__device__ __forceinline__ unsigned load_flags16_ordered(const uint8_t *flags,
+                                                         const int64_t *order, int64_t base,
+                                                         int64_t n) {
+    unsigned bits = 0;
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+        if (base + k < n && __ldg(flags + __ldg(order + base + k))) bits |= 1u << k;
+    return bits;
+}
+
+__device__ __forceinline__ const int64_t *active_order(const int64_t *order, const int *ident) {
+    return (order && !(ident && *ident)) ? order : nullptr;
+}
+
 __device__ __forceinline__ int block_sum(int v, int *red) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     v = __reduce_add_sync(0xffffffffu, v);
@@ -48,10 +67,13 @@ __device__ __forceinline__ int block_sum(int v, int *red) {
 }
 
 __global__ void __launch_bounds__(kThreads)
-compact_count_kernel(const uint8_t *flags, int64_t n, int64_t *tile_count) {
+compact_count_kernel(const uint8_t *flags, int64_t n, int64_t *tile_count,
+                     const int64_t *order, const int *ident) {
     __shared__ int red[kThreads / 32];
     const int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)threadIdx.x * kPerThread;
-    const int c = __popc(load_flags16(flags, base, n));
+    const int64_t *ord = active_order(order, ident);
+    const int c = __popc(ord ? load_flags16_ordered(flags, ord, base, n)
+                             : load_flags16(flags, base, n));
     const int t = block_sum(c, red);
     if (threadIdx.x == 0) tile_count[blockIdx.x] = t;
 }
@@ -95,11 +117,13 @@ compact_scan_kernel(int64_t *tile_count, int64_t ntiles, int64_t *n_out) {
 }
 
 __global__ void __launch_bounds__(kThreads)
-compact_scatter_kernel(const uint8_t *flags, int64_t n, const int64_t *tile_off, int64_t *idx) {
+compact_scatter_kernel(const uint8_t *flags, int64_t n, const int64_t *tile_off, int64_t *idx,
+                       const int64_t *order, const int *ident) {
     __shared__ int warp_tot[kThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)threadIdx.x * kPerThread;
-    unsigned bits = load_flags16(flags, base, n);
+    const int64_t *ord = active_order(order, ident);
+    unsigned bits = ord ? load_flags16_ordered(flags, ord, base, n) : load_flags16(flags, base, n);
     const int c = __popc(bits);
     int x = c;
 #pragma unroll
@@ -115,7 +139,7 @@ compact_scatter_kernel(const uint8_t *flags, int64_t n, const int64_t *tile_off,
     while (bits) {
         const int k = __ffs(bits) - 1;
         bits &= bits - 1;
-        idx[out++] = base + k;
+        idx[out++] = ord ? __ldg(ord + base + k) : base + k;
     }
 }
 
@@ -124,12 +148,15 @@ compact_scatter_kernel(const uint8_t *flags, int64_t n, const int64_t *tile_off,
 int64_t compact_tiles(int64_t n) { return (n + kTile - 1) / kTile; }
 
 cudaError_t launch_compact(const uint8_t *flags, int64_t n, int64_t *idx, int64_t *n_out,
-                           int64_t *tile_scratch, cudaStream_t st) {
+                           int64_t *tile_scratch, cudaStream_t st, const int64_t *order,
+                           const int *ident) {
     const int64_t ntiles = compact_tiles(n);
     if (ntiles == 0) return cudaMemsetAsync(n_out, 0, sizeof(int64_t), st);
-    compact_count_kernel<<<(unsigned)ntiles, kThreads, 0, st>>>(flags, n, tile_scratch);
+    compact_count_kernel<<<(unsigned)ntiles, kThreads, 0, st>>>(flags, n, tile_scratch, order,
+                                                                ident);
     compact_scan_kernel<<<1, 1024, 0, st>>>(tile_scratch, ntiles, n_out);
-    compact_scatter_kernel<<<(unsigned)ntiles, kThreads, 0, st>>>(flags, n, tile_scratch, idx);
+    compact_scatter_kernel<<<(unsigned)ntiles, kThreads, 0, st>>>(flags, n, tile_scratch, idx,
+                                                                  order, ident);
     return cudaGetLastError();
 }
 

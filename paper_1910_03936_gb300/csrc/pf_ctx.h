@@ -56,6 +56,9 @@ struct pf_ctx {
     // of scratch, 2 zero (the last pf_filter_verify had no pairs)
     int verified_state = 0;
     int grid_cache[4][pf::kNumBatchCfgs] = {};
+    // the last run_filter grouped its pairs: the scratch's order (unless
+    // *ident) lists them by configuration and length class
+    bool binned = false;
 
     cudaStream_t side_streams[pf::kSideStreams] = {};
     cudaEvent_t ev_fork = nullptr;

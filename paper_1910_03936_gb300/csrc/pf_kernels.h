@@ -80,6 +80,14 @@ constexpr bool cfg_serves(const KernelCfg &c, int E) {
     return c.xe >= 0 ? c.xe == E : c.ecap >= E;
 }
 constexpr int kNumBatchCfgs = sizeof(kBatchCfgs) / sizeof(kBatchCfgs[0]);
+// Inside a configuration's bin the scheduler groups pairs by length class
+// (ceil(len/32) words, the last class holding 8 words and more): keys of
+// the binning counting sort.
+constexpr int kLenClasses = 9;
+constexpr int kNumBinKeys = kNumBatchCfgs * kLenClasses;
+// Work counters in the scheduler's scratch: one per configuration's bin,
+// then the verifier's.
+constexpr int kWorkCounters = kNumBatchCfgs + 1;
 constexpr int kFirstExactCfg = 20;  // kBatchCfgs[20 + E] serves exactly E
 
 // Plain kernel (one thread per pair): DPT = kPlainDpt[i] serves E <= DPT - 1.
@@ -107,10 +115,14 @@ cudaError_t launch_pack_fixed(const uint8_t *ascii, int64_t nseq, int len, uint3
                               uint32_t *hi, uint32_t *nm, unsigned *err, int sms,
                               cudaStream_t st);
 int64_t compact_tiles(int64_t n);
+// order (may be null; used unless *ident): position q stands for pair
+// order[q], and the indices come out in that order.
 cudaError_t launch_compact(const uint8_t *flags, int64_t n, int64_t *idx, int64_t *n_out,
-                           int64_t *tile_scratch, cudaStream_t st);
+                           int64_t *tile_scratch, cudaStream_t st,
+                           const int64_t *order = nullptr, const int *ident = nullptr);
 cudaError_t launch_verify(const PairsView &pv, const int32_t *lens, const int16_t *E, int E_max,
                           const int64_t *idx, const int64_t *n_idx, int64_t n, int32_t *dist,
-                          unsigned *err, int sms, cudaStream_t st);
+                          unsigned *err, int sms, cudaStream_t st,
+                          unsigned long long *work = nullptr);
 
 }  // namespace pf

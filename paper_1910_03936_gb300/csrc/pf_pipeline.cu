@@ -90,8 +90,8 @@ pf_status alloc_slot(Job &J, Slot &s) {
     const size_t o_acc = add(sl * C), o_cnt = add(sl * C * 2), o_dist = add(C * 4);
     const size_t o_ord = add(C * 8), o_idx = add(C * 8), o_nidx = add(8),
                  o_tiles = add((size_t)compact_tiles((int64_t)C) * 8),
-                 o_bins = add((kNumBatchCfgs + 1) * 8), o_work = add(kNumBatchCfgs * 8),
-                 o_hist = add(kNumBatchCfgs * 8), o_cur = add(kNumBatchCfgs * 8),
+                 o_bins = add((kNumBatchCfgs + 1) * 8), o_work = add(kWorkCounters * 8),
+                 o_hist = add(kNumBinKeys * 8), o_cur = add(kNumBinKeys * 8),
                  o_ident = add(4), o_need = add(C);
     if (cudaMalloc(&s.mem, o) != cudaSuccess) {
         cudaGetLastError();
@@ -178,10 +178,11 @@ pf_status enqueue_chunk(Job &J, Slot &s, int64_t nc) {
     pf_status st = ctx->run_filter(J.dec, a, s.scr);
     ctx->stream = saved;
     if (st != PF_OK) return st;
-    e = launch_compact(a.need ? a.need : s.acc, nc, s.scr.idx, s.scr.n_idx, s.scr.tiles, s.st);
+    e = launch_compact(a.need ? a.need : s.acc, nc, s.scr.idx, s.scr.n_idx, s.scr.tiles, s.st,
+                       ctx->binned ? s.scr.order : nullptr, s.scr.ident);
     if (e == cudaSuccess)
         e = launch_verify(pv, s.lens, a.E, J.E_max, s.scr.idx, s.scr.n_idx, nc, s.dist,
-                          ctx->d_err, ctx->sms, s.st);
+                          ctx->d_err, ctx->sms, s.st, s.scr.work + kNumBatchCfgs);
     return ctx->cuda(e, "pf_run_host launch");
 }
 

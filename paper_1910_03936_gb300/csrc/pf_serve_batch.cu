@@ -398,10 +398,11 @@ pf_status launch(ServeState &S, BatchSlot &b) {
     pf_status s = sub->run_filter(b.dec, a, B.scr);
     if (s != PF_OK) return s;
     cudaEventRecord(b.ev_phase[2], st);
-    e = launch_compact(a.need ? a.need : B.acc, P, B.scr.idx, B.scr.n_idx, B.scr.tiles, st);
+    e = launch_compact(a.need ? a.need : B.acc, P, B.scr.idx, B.scr.n_idx, B.scr.tiles, st,
+                       sub->binned ? B.scr.order : nullptr, B.scr.ident);
     if (e == cudaSuccess)
         e = launch_verify(pv, B.lens, B.E, b.E_max, B.scr.idx, B.scr.n_idx, P, B.dist, sub->d_err,
-                          sub->sms, st);
+                          sub->sms, st, B.scr.work + kNumBatchCfgs);
     cudaEventRecord(b.ev_phase[3], st);
     if (e == cudaSuccess) {
         batch_epilogue_kernel<<<grid, 256, 0, st>>>(b.d_segs, ns, P, b.dec, B.seg_of, B.acc,
@@ -484,8 +485,8 @@ pf_status batch_start(pf_ctx *ctx, ServeState *Sp) {
     for (auto &x : o_pl) x = add((size_t)B.W * 4);
     const size_t o_ord = add(nn * 8), o_idx = add(nn * 8), o_nidx = add(8),
                  o_tiles = add((size_t)compact_tiles(P) * 8),
-                 o_bins = add((kNumBatchCfgs + 1) * 8), o_work = add(kNumBatchCfgs * 8),
-                 o_hist = add(kNumBatchCfgs * 8), o_cur = add(kNumBatchCfgs * 8),
+                 o_bins = add((kNumBatchCfgs + 1) * 8), o_work = add(kWorkCounters * 8),
+                 o_hist = add(kNumBinKeys * 8), o_cur = add(kNumBinKeys * 8),
                  o_ident = add(4), o_need = add(nn);
     size_t o_rd[kBatchSlots], o_rf[kBatchSlots], o_sg[kBatchSlots], o_ro[kBatchSlots],
         o_re[kBatchSlots];
