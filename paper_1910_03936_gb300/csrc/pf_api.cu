@@ -648,9 +648,14 @@ pf_status pf_ctx::run_filter(unsigned dec, const FilterArgs &a, const Scratch &s
         plain = true;
         for (int e = a.E ? 0 : a.E_max; e <= a.E_max && plain; ++e) plain = tune_plain[dec][e];
     }
-    if (plain)
+    if (plain) {
+        // one threshold for the whole batch: the plain kernel with it fixed
+        // at compile time (every shift and liveness test a constant)
+        if (!a.E && a.E_max <= kPlainExactMaxE)
+            return cuda(launch_filter_plain_exact((int)dec, a.E_max, a, stream), "filter launch");
         return cuda(launch_filter_plain((int)dec, plain_index(a.E_max), a, stream),
                     "filter launch");
+    }
     return run_batched(dec, a, s);
 }
 

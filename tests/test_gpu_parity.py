@@ -777,6 +777,15 @@ def test_small_batches_take_one_plain_launch(pf, case_data):
         pf.pf_sync(c)
         want = np.where(oa[0] == 1, oracle.verify_batch(P), P.E.astype(np.int32) + 1)
         assert np.array_equal(dist.cpu().numpy(), want)
+        # one threshold for the whole batch (no per-pair E): the plain kernel
+        # with the threshold fixed at compile time (E <= 15), else at run time
+        for name in ("cfg1_uniform_100bp_E5", "cfg2_150bp_E0", "cfg2_150bp_E15",
+                     "cfg4_250bp_E25"):
+            P2, D2, (oa2, oc2) = case_data[name]
+            for dec in (1, 2, 3):
+                a2, k2 = filter_dev(c, D2, dec, per_pair_E=False)
+                rows = [0, 1] if dec == 3 else [dec - 1]
+                assert np.array_equal(k2, oc2[rows]) and np.array_equal(a2, oa2[rows]), (name, dec)
         with pytest.raises(pf.PFError):
             pf.pf_set_small_batch(c, -1)
     finally:
