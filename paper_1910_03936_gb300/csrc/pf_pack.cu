@@ -69,40 +69,41 @@ __device__ __forceinline__ void decode_chunks(uintptr_t cbase, int nchunks, uint
 }
 
 // Ragged layout: block handles sequences [s0, s0 + kSeqPerBlock); its
-// threads walk the block's words, finding each word's sequence by a binary
-// search over the staged word offsets, and decode each word from its own
-// 32-byte window.  (Decoding the block's bytes as one chunk stream first, as
-// the fixed layout does, was slower here: the extra round of memory latency
-// for the offsets and the binary search per word left too little work per
-// block to hide it.)  Words past ceil(len/32) of a sequence (a word_off
-// with room to spare) are all N.  With seg_of given, a byte error of
-// sequence s is recorded in seg_err[seg_of[s]] instead of err (the serving
-// batches attribute errors to the request a sequence came from).
+// threads walk the block's words, each decoding its word from its own
+// 32-byte window.  A word's sequence comes from a map in shared memory
+// (one byte per word, written by the sequences' threads; a block whose
+// sequences hold more than kMapCap words searches the staged offsets
+// instead).  (Decoding the block's bytes as one chunk stream first, as the
+// fixed layout does, was slower here: the extra round of memory latency for
+// the offsets left too little work per block to hide it.)  Words past
+// ceil(len/32) of a sequence (a word_off with room to spare) are all N.
+// With seg_of given, a byte error of sequence s is recorded in
+// seg_err[seg_of[s]] instead of err (the serving batches attribute errors
+// to the request a sequence came from).
 //
 // STARTS: word_off holds each sequence's first word, in any order (a layout
 // that groups sequences by threshold and length); the block lays its
 // sequences' ceil(len/32) words out locally (a prefix sum by one warp) and
 // writes word w of sequence s to word_off[s] + w.
-constexpr int kSeqPerBlock = 128;
+constexpr int kSeqPerBlock = 256;
+constexpr int kMapCap = 16 * kSeqPerBlock;
 
+// Six blocks per SM: at eight the kernel's 32 registers spill.
 template <bool STARTS>
-__global__ void __launch_bounds__(kPackThreads, 8)
+__global__ void __launch_bounds__(kPackThreads, 6)
 pack_ragged_kernel(const uint8_t *ascii, const int64_t *byte_off, const int64_t *word_off,
                    int64_t nseq, uint32_t *lo, uint32_t *hi, uint32_t *nm, unsigned *err,
                    const int32_t *seg_of, unsigned *seg_err) {
-    __shared__ int64_t woff[kSeqPerBlock + 1];  // first word of each sequence, rising
-    __shared__ int64_t wdst[STARTS ? kSeqPerBlock : 1];
+    __shared__ int woff[kSeqPerBlock + 1];       // block-local first word, rising
+    __shared__ int64_t wdst[kSeqPerBlock + 1];   // first word in the planes
     __shared__ int64_t boff[kSeqPerBlock + 1];
     __shared__ int32_t sseg[kSeqPerBlock];
+    __shared__ uint8_t wseq[kMapCap];            // local word -> local sequence
     const int64_t s0 = (int64_t)blockIdx.x * kSeqPerBlock;
     const int ns = (int)min((int64_t)kSeqPerBlock, nseq - s0);
     for (int i = threadIdx.x; i <= ns; i += blockDim.x) {
         boff[i] = byte_off[s0 + i];
-        if constexpr (STARTS) {
-            if (i < ns) wdst[i] = word_off[s0 + i];
-        } else {
-            woff[i] = word_off[s0 + i];
-        }
+        if (!STARTS || i < ns) wdst[i] = word_off[s0 + i];
         if (seg_of && i < ns) sseg[i] = seg_of[s0 + i];
     }
     __syncthreads();
@@ -133,20 +134,31 @@ pack_ragged_kernel(const uint8_t *ascii, const int64_t *byte_off, const int64_t 
             }
             if (lane == 31) woff[kSeqPerBlock] = inc;
         }
-        __syncthreads();
+    } else {
+        for (int i = threadIdx.x; i <= ns; i += blockDim.x) woff[i] = (int)(wdst[i] - wdst[0]);
     }
+    __syncthreads();
+    const int total = woff[ns];
+    const bool direct = total <= kMapCap;
+    if (direct)
+        for (int i = threadIdx.x; i < ns; i += blockDim.x)
+            for (int j = woff[i]; j < woff[i + 1]; ++j) wseq[j] = (uint8_t)i;
+    __syncthreads();
     const uint8_t *lim = ascii + __ldg(byte_off + nseq);
-    const int64_t base = woff[0];
-    const int total = (int)(woff[ns] - base);
     for (int j = threadIdx.x; j < total; j += blockDim.x) {
-        const int64_t gw = base + j;
-        int l = 0, r = ns - 1;  // last sequence with woff <= gw
-        while (l < r) {
-            const int mid = (l + r + 1) >> 1;
-            if (woff[mid] <= gw) l = mid; else r = mid - 1;
+        int l;
+        if (direct) {
+            l = wseq[j];
+        } else {  // last sequence with woff <= j
+            int r = ns - 1;
+            l = 0;
+            while (l < r) {
+                const int mid = (l + r + 1) >> 1;
+                if (woff[mid] <= j) l = mid; else r = mid - 1;
+            }
         }
-        const int w = (int)(gw - woff[l]);
-        const int64_t dst = STARTS ? wdst[l] + w : gw;
+        const int w = j - woff[l];
+        const int64_t dst = STARTS ? wdst[l] + w : wdst[0] + j;
         const int len = (int)(boff[l + 1] - boff[l]);
         if (len - 32 * w <= 0) {
             lo[dst] = 0u;
