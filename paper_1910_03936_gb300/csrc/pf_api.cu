@@ -281,12 +281,16 @@ int pf::pf_default_cfg(int E) {
         for (int c = 0; c < kNumBatchCfgs; ++c)
             if (kBatchCfgs[c].xe == E && kBatchCfgs[c].words >= 8) return c;
     if (E <= 15) return kFirstExactCfg + E;
-    // eight lanes per pair, the fewest slots that hold the 2E+1 diagonals
+    // the two-phase form with two or four lanes per pair and the fewest
+    // slots that hold the 2E+1 diagonals (four lanes on a tie)
     int best = -1;
-    for (int c = 0; c < kNumBatchCfgs; ++c)
-        if (kBatchCfgs[c].tpp == 8 && kBatchCfgs[c].xe < 0 && kBatchCfgs[c].ecap >= E &&
-            kBatchCfgs[c].words >= 8 && (best < 0 || kBatchCfgs[c].ecap < kBatchCfgs[best].ecap))
+    for (int c = 0; c < kNumBatchCfgs; ++c) {
+        const KernelCfg &k = kBatchCfgs[c];
+        if ((k.tpp != 2 && k.tpp != 4) || k.xe >= 0 || k.ecap < E || k.words < 8) continue;
+        if (best < 0 || k.ecap < kBatchCfgs[best].ecap ||
+            (k.ecap == kBatchCfgs[best].ecap && k.tpp > kBatchCfgs[best].tpp))
             best = c;
+    }
     return best;
 }
 

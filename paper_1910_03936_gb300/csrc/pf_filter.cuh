@@ -119,6 +119,21 @@ struct PairFilter {
         return d <= E && -d <= E;
     }
 
+    // Lane groups with the threshold known at run time: a slot whose
+    // diagonal lies outside the band holds all-ones mask words (a diagonal
+    // blocked at every column).  Neither decider can tell such a diagonal
+    // from none: SneakySnake's AND of (y | -y) keeps every bit at or after
+    // the checkpoint of an all-ones y, GateKeeper's amend leaves an all-ones
+    // word as it is.  So only the map looks at liveness (once per pair, as
+    // a bit per slot), and every other loop runs all slots unconditionally.
+    static constexpr bool ONES = (TPP > 1) && (XE < 0);
+    uint32_t dead_bits;   // ONES: bit k set when slot k is outside the band
+
+    __device__ __forceinline__ bool skip(int k, int g) const {
+        if constexpr (ONES) return false;
+        else return !live(k, g);
+    }
+
     // the threshold, a constant in the exact-threshold form
     __device__ __forceinline__ int thr() const {
         if constexpr (XE >= 0) return XE;
@@ -159,6 +174,12 @@ struct PairFilter {
 
     // Process every remaining word, then leave `role` for finish().
     __device__ __forceinline__ void run(const PairsView &pv, int g, unsigned gmask) {
+        if constexpr (ONES) {
+            dead_bits = 0u;
+#pragma unroll
+            for (int k = 0; k < NS; ++k)
+                if (!live(k, g)) dead_bits |= 1u << k;
+        }
         if constexpr (!GK) {  // no history to rotate
             while (!done()) word(pv, g, gmask, P0, P2, P1);
         } else {
@@ -191,7 +212,7 @@ struct PairFilter {
         }
 #pragma unroll
         for (int k = 0; k < NS; ++k) {
-            if (!live(k, g)) continue;
+            if (skip(k, g)) continue;
             const int d = slot_d<TPP, DPT, XE>(k, g);
             uint32_t slo, shi, snm;
             if constexpr (TPP == 1) {
@@ -210,12 +231,14 @@ struct PairFilter {
                 snm = shr_pair(A.nm, B.nm, d);
             }
             M[k] = (F.lo ^ slo) | (F.hi ^ shi) | F.nm | snm;
+            if constexpr (ONES)  // all ones outside the band
+                M[k] |= (uint32_t)((int32_t)(dead_bits << (31 - k)) >> 31);
         }
         if (w == W - 1 && (m & 31)) {  // columns >= m of the last word are not cells
             const uint32_t valid = (1u << (m & 31)) - 1u;
 #pragma unroll
             for (int k = 0; k < NS; ++k)
-                if (live(k, g)) M[k] &= valid;
+                if (!skip(k, g)) M[k] &= valid;
         }
         if constexpr (SINK) {
 #pragma unroll
@@ -230,7 +253,7 @@ struct PairFilter {
                     uint32_t T = 0xffffffffu;
 #pragma unroll
                     for (int k = 0; k < NS; ++k) {
-                        if (!live(k, g)) continue;
+                        if (skip(k, g)) continue;
                         const uint32_t y = M[k] | (uint32_t)((dead >> k) & 1u);
                         T &= (y | (y * neg1));
                     }
@@ -241,7 +264,7 @@ struct PairFilter {
                         } else {
 #pragma unroll
                             for (int k = 0; k < NS; ++k)
-                                if (live(k, g) && M[k]) dead |= Mask(1) << k;
+                                if (!skip(k, g) && M[k]) dead |= Mask(1) << k;
                         }
                         word_done = true;
                     } else {
@@ -263,7 +286,7 @@ struct PairFilter {
                     uint32_t T = 0xffffffffu;
 #pragma unroll
                     for (int k = 0; k < NS; ++k) {
-                        if (!live(k, g)) continue;
+                        if (skip(k, g)) continue;
                         const uint32_t y = M[k] & C;
                         T &= (y | (y * neg1));
                     }
@@ -275,7 +298,7 @@ struct PairFilter {
                             Mask dd = 0u;
 #pragma unroll
                             for (int k = 0; k < NS; ++k)
-                                if (live(k, g) && (M[k] & C)) dd |= Mask(1) << k;
+                                if (!skip(k, g) && (M[k] & C)) dd |= Mask(1) << k;
                             dead = dd;
                             cont = true;
                         }
@@ -313,7 +336,7 @@ struct PairFilter {
                     uint32_t Fa = 0xffffffffu;
 #pragma unroll
                     for (int k = 0; k < NS; ++k) {
-                        if (!live(k, g)) continue;
+                        if (skip(k, g)) continue;
                         const uint32_t H = Mp[k];
                         const uint32_t l1 = __funnelshift_l(Mpp[k], H, 1);
                         const uint32_t l2 = __funnelshift_l(Mpp[k], H, 2);
@@ -355,7 +378,7 @@ struct PairFilter {
                 uint32_t Fa = 0xffffffffu;
 #pragma unroll
                 for (int k = 0; k < NS; ++k) {
-                    if (!live(k, g)) continue;
+                    if (skip(k, g)) continue;
                     const uint32_t H = Mp[k];
                     const uint32_t l1 = __funnelshift_l(Mpp[k], H, 1);
                     const uint32_t l2 = __funnelshift_l(Mpp[k], H, 2);
@@ -628,15 +651,11 @@ template <int TPP, int DPT>
 __device__ __forceinline__ int split_sneakysnake_group(const uint32_t *mine, int W, int E, int g,
                                                        unsigned gmask, uint32_t neg1) {
     if (W == 0) return 0;
-    unsigned live = 0u;  // this lane's live slots
-#pragma unroll
-    for (int k = 0; k < DPT; ++k) {
-        const int d = slot_d<TPP, DPT, -1>(k, g);
-        if (d <= E && -d <= E) live |= 1u << k;
-    }
+    // slots outside the band were stored as all ones (PairFilter::ONES):
+    // neutral in the AND below, so every slot takes part
     uint32_t Mw[DPT];
 #pragma unroll
-    for (int k = 0; k < DPT; ++k) Mw[k] = ((live >> k) & 1u) ? mine[k * 32] : 0u;
+    for (int k = 0; k < DPT; ++k) Mw[k] = mine[k * 32];
     int ws = 0, kss = 0;
     uint32_t C = 0xffffffffu;
     for (;;) {
@@ -645,7 +664,7 @@ __device__ __forceinline__ int split_sneakysnake_group(const uint32_t *mine, int
 #pragma unroll
         for (int k = 0; k < DPT; ++k) {
             y[k] = Mw[k] & C;
-            if ((live >> k) & 1u) T &= y[k] | (y[k] * neg1);
+            T &= y[k] | (y[k] * neg1);
         }
         T = group_and<TPP>(T, gmask);
         const int pbit = __ffs(T) - 1;  // the obstacle passed; -1 if T == 0
@@ -660,8 +679,7 @@ __device__ __forceinline__ int split_sneakysnake_group(const uint32_t *mine, int
         ++ws;
         const uint32_t cm = (T == 0u) ? 1u : 0u;
 #pragma unroll
-        for (int k = 0; k < DPT; ++k)
-            Mw[k] = ((live >> k) & 1u) ? (mine[(ws * DPT + k) * 32] | min(y[k], cm)) : 0u;
+        for (int k = 0; k < DPT; ++k) Mw[k] = mine[(ws * DPT + k) * 32] | min(y[k], cm);
         C = 0xffffffffu;
     }
     return kss > E + 1 ? E + 1 : kss;

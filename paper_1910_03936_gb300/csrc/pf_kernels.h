@@ -51,9 +51,9 @@ constexpr KernelCfg kBatchCfgs[] = {
     // E = 8..13: 68 KB (three blocks per SM) to 108 KB (two) per block
     {1, 9, 8, 8, 8},     {1, 10, 9, 9, 8},    {1, 11, 10, 10, 8},  {1, 12, 11, 11, 8},
     {1, 13, 12, 12, 8},  {1, 14, 13, 13, 8},
-    // lane groups of two and four (fewer shuffles per step; with both
-    // deciders the fastest at E = 16..25)
-    {2, 17, 16, -1, 8},  {4, 11, 21, -1, 8},  {4, 13, 25, -1, 8},
+    // lane groups of two and four (fewer shuffles per step, the walk's
+    // control repeated by fewer lanes): the fastest at E = 16..31
+    {2, 17, 16, -1, 8},  {4, 11, 21, -1, 8},  {4, 13, 25, -1, 8},  {2, 26, 25, -1, 8},
 };
 
 // The two-phase form applies where SneakySnake runs (deciders 1 and 3);
