@@ -757,7 +757,8 @@ pf_status pf_filter_verify(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs
                    "compact launch");
     if (st != PF_OK) return st;
     st = ctx->cuda(launch_verify(to_view(pairs), lens, E, E_max, s.idx, s.n_idx, n, dist,
-                                 ctx->d_err, ctx->sms, ctx->stream, s.work + kNumBatchCfgs),
+                                 ctx->d_err, ctx->sms, ctx->stream, s.work + kNumBatchCfgs,
+                                 ctx->binned),
                    "verify launch");
     ctx->verified_state = (st == PF_OK) ? 1 : 0;
     return st;

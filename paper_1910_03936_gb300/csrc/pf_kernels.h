@@ -123,6 +123,6 @@ cudaError_t launch_compact(const uint8_t *flags, int64_t n, int64_t *idx, int64_
 cudaError_t launch_verify(const PairsView &pv, const int32_t *lens, const int16_t *E, int E_max,
                           const int64_t *idx, const int64_t *n_idx, int64_t n, int32_t *dist,
                           unsigned *err, int sms, cudaStream_t st,
-                          unsigned long long *work = nullptr);
+                          unsigned long long *work = nullptr, bool grouped = false);
 
 }  // namespace pf

@@ -182,7 +182,7 @@ pf_status enqueue_chunk(Job &J, Slot &s, int64_t nc) {
                        ctx->binned ? s.scr.order : nullptr, s.scr.ident);
     if (e == cudaSuccess)
         e = launch_verify(pv, s.lens, a.E, J.E_max, s.scr.idx, s.scr.n_idx, nc, s.dist,
-                          ctx->d_err, ctx->sms, s.st, s.scr.work + kNumBatchCfgs);
+                          ctx->d_err, ctx->sms, s.st, s.scr.work + kNumBatchCfgs, ctx->binned);
     return ctx->cuda(e, "pf_run_host launch");
 }
 

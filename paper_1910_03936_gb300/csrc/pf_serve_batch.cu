@@ -402,7 +402,7 @@ pf_status launch(ServeState &S, BatchSlot &b) {
                        sub->binned ? B.scr.order : nullptr, B.scr.ident);
     if (e == cudaSuccess)
         e = launch_verify(pv, B.lens, B.E, b.E_max, B.scr.idx, B.scr.n_idx, P, B.dist, sub->d_err,
-                          sub->sms, st, B.scr.work + kNumBatchCfgs);
+                          sub->sms, st, B.scr.work + kNumBatchCfgs, sub->binned);
     cudaEventRecord(b.ev_phase[3], st);
     if (e == cudaSuccess) {
         batch_epilogue_kernel<<<grid, 256, 0, st>>>(b.d_segs, ns, P, b.dec, B.seg_of, B.acc,
