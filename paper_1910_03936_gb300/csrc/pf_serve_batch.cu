@@ -185,6 +185,7 @@ struct BatchSlot {
     unsigned dec = 0;
     int E_max = 0;
     bool full = false;
+    bool closed = false;  // its uploads end here: segment table sent, ev_copied recorded
     bool failed = false;  // its launch failed: nothing it holds is valid
     cudaEvent_t ev_copied = nullptr, ev_enq = nullptr, ev_start = nullptr, ev_done = nullptr;
     cudaEvent_t ev_phase[4] = {};       // after offsets, pack, filter, verification
@@ -197,6 +198,7 @@ struct BatchSlot {
         dec = 0;
         E_max = 0;
         full = false;
+        closed = false;
         failed = false;
     }
 };
@@ -350,6 +352,20 @@ void place(ServeState &S, BatchSlot &b, const std::shared_ptr<ServeReq> &qp, int
     if (b.pairs >= B.P || b.nseg >= kMaxSegs) b.full = true;
 }
 
+// The batch takes no more placements: its segment table joins its uploads
+// on the copy stream (a copy issued on the compute stream would queue in the
+// copy engine behind the uploads of later batches), and ev_copied marks the
+// end of its uploads there, before any of the next batch's.  Recorded when
+// the batch fills up, so that its launch does not also wait for the uploads
+// placed into the next batch in the meantime.
+void close_uploads(BatchPool &B, BatchSlot &b) {
+    if (b.closed) return;
+    cudaMemcpyAsync(b.d_segs, b.h_segs, sizeof(SegDesc) * (size_t)b.nseg, cudaMemcpyHostToDevice,
+                    B.s_copy);
+    cudaEventRecord(b.ev_copied, B.s_copy);
+    b.closed = true;
+}
+
 // The batch's device work on the compute stream.
 pf_status launch(ServeState &S, BatchSlot &b) {
     BatchPool &B = *S.bp;
@@ -357,13 +373,8 @@ pf_status launch(ServeState &S, BatchSlot &b) {
     cudaStream_t st = B.s_compute;
     const int64_t P = b.pairs;
     const int ns = b.nseg;
-    // the segment table joins the batch's uploads on the copy stream: a copy
-    // issued on the compute stream would queue in the copy engine behind the
-    // uploads of later batches (milliseconds under load)
-    cudaMemcpyAsync(b.d_segs, b.h_segs, sizeof(SegDesc) * (size_t)ns, cudaMemcpyHostToDevice,
-                    B.s_copy);
+    close_uploads(B, b);
     cudaEventRecord(b.ev_enq, st);
-    cudaEventRecord(b.ev_copied, B.s_copy);
     cudaStreamWaitEvent(st, b.ev_copied, 0);
     cudaEventRecord(b.ev_start, st);
     const unsigned grid =
@@ -733,6 +744,7 @@ void batch_scheduler(ServeState *Sp) {
                 if (q.next == q.req.n) queue.pop_front();
             }
             if (b.full) {  // waits for the GPU; the next slot opens
+                close_uploads(B, b);
                 B.ready.push_back(B.open);
                 B.open = -1;
             }
