@@ -42,6 +42,22 @@ METRIC = "pairs/s (SneakySnake, 150bp, E=6) batched vs plain kernel; serve p50/p
 WORKLOAD = "cfg2_150bp_E6_20M"
 
 
+
+def host_copy(pf, a):
+    """A copy of numpy array a in page-locked host memory from pf_host_alloc
+    (huge pages: uploads from it do not stall), as a torch tensor."""
+    import torch
+    h = pf.host_empty(a.size, a.dtype)
+    h[:] = a.reshape(-1)
+    return torch.from_numpy(h)
+
+
+def host_zeros(pf, count, dtype):
+    import torch
+    h = pf.host_empty(count, torch.empty(0, dtype=dtype).numpy().dtype)
+    h[:] = 0
+    return torch.from_numpy(h)
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -234,7 +250,7 @@ def serve_reference_rates(pf, ctx, seed, n=4_000_000):
     import synth
     dev = torch.device("cuda", 0)
     P = synth.generate(synth.SERVE, seed + 99, n, kmax=60)
-    reads_h = torch.from_numpy(P.reads).pin_memory()
+    reads_h = host_copy(pf, P.reads)
     reads = reads_h.to(dev)
     refs = torch.from_numpy(P.refs).to(dev)
     wo, total = pf.pf_pack_layout(P.read_off)
@@ -558,8 +574,8 @@ def run_other_workload(args):
                            kmax=100)
         fixed, Emax, kind = 250, 25, "skewed_all"
     n = P.n
-    reads_h = torch.from_numpy(P.reads).pin_memory()
-    refs_h = torch.from_numpy(P.refs).pin_memory()
+    reads_h = host_copy(pf, P.reads)
+    refs_h = host_copy(pf, P.refs)
     reads, refs = reads_h.to(dev), refs_h.to(dev)
     lens = torch.from_numpy(P.lens).to(dev)
     E = torch.from_numpy(P.E).to(dev)
@@ -622,14 +638,14 @@ def run_other_workload(args):
     out["unit"] = "pairs/s"
     if w == "cfg3":  # chunked host pipeline, graph replay, pinned host buffers
         import time
-        acc_h = torch.empty(2 * n, dtype=torch.uint8).pin_memory().numpy()
-        cnt_h = torch.empty(2 * n, dtype=torch.int16).pin_memory().numpy()
-        dist_h = torch.empty(n, dtype=torch.int32).pin_memory().numpy()
+        acc_h = host_zeros(pf, 2 * n, torch.uint8).numpy()
+        cnt_h = host_zeros(pf, 2 * n, torch.int16).numpy()
+        dist_h = host_zeros(pf, n, torch.int32).numpy()
         args_rh = (ctx, 3, reads_h.numpy(), refs_h.numpy(), Emax)
         # offsets and thresholds pinned too: a pageable source makes its
         # upload synchronous and stalls the overlap of the two slots
-        off_h = torch.from_numpy(P.read_off).pin_memory().numpy()
-        E_h = torch.from_numpy(P.E).pin_memory().numpy()
+        off_h = host_copy(pf, P.read_off).numpy()
+        E_h = host_copy(pf, P.E).numpy()
         kw = dict(byte_off=off_h, E=E_h, chunk_pairs=1 << 21, out=(acc_h, cnt_h, dist_h))
         pf.pf_run_host(*args_rh, **kw)
         runs = []
@@ -679,8 +695,8 @@ def main_gpu(args):
 
     ctx = pf.pf_create(local)
     stream = torch.cuda.current_stream(dev)
-    reads_h = torch.from_numpy(P.reads).pin_memory()
-    refs_h = torch.from_numpy(P.refs).pin_memory()
+    reads_h = host_copy(pf, P.reads)
+    refs_h = host_copy(pf, P.refs)
     reads = reads_h.to(dev)
     refs = refs_h.to(dev)
     del P
@@ -693,9 +709,9 @@ def main_gpu(args):
     acc = torch.empty(2 * n, dtype=torch.uint8, device=dev)
     cnt = torch.empty(2 * n, dtype=torch.int16, device=dev)
     dist_out = torch.empty(n, dtype=torch.int32, device=dev)
-    acc_h = torch.empty(2 * n, dtype=torch.uint8).pin_memory()
-    cnt_h = torch.empty(2 * n, dtype=torch.int16).pin_memory()
-    dist_h = torch.empty(n, dtype=torch.int32).pin_memory()
+    acc_h = host_zeros(pf, 2 * n, torch.uint8)
+    cnt_h = host_zeros(pf, 2 * n, torch.int16)
+    dist_h = host_zeros(pf, n, torch.int32)
 
     # tune the batched kernel for this threshold on a sample of the batch
     pf.pf_pack_fixed(ctx, reads, n, M, rd)
@@ -887,7 +903,8 @@ def main_gpu(args):
     # device work replayed as a CUDA graph
     out_bufs = (acc_h.numpy(), cnt_h.numpy(), dist_h.numpy())
     rh, fh = reads_h.numpy(), refs_h.numpy()
-    E_h = torch.full((n,), E_HEAD, dtype=torch.int16).pin_memory().numpy()
+    E_h = host_zeros(pf, n, torch.int16).numpy()
+    E_h[:] = E_HEAD
     pf.pf_run_host(ctx, 3, rh, fh, E_HEAD, length=M, E=E_h, chunk_pairs=1 << 20, out=out_bufs)
     e2e_steps = max(1, min(args.steps, 3))
     if dist is not None:

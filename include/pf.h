@@ -397,6 +397,27 @@ PF_API pf_status pf_filter_verify(pf_ctx *ctx, unsigned deciders, const pf_pairs
  * if a later call on the context reallocated its scratch memory. */
 PF_API pf_status pf_last_verified_count(pf_ctx *ctx, int64_t *n_verified);
 
+/* ---- host memory for the host-buffer calls ------------------------------- */
+
+/* Page-locked host memory backed by 2 MB pages where the system has them.
+ * Blocks are carved out of a few large regions (at least 1 GB each; Linux:
+ * an anonymous mapping advised for transparent huge pages, registered with
+ * cudaHostRegister once) that live for the rest of the process; a freed
+ * block's space is reused.  Meant for the buffers pf_run_host and serving
+ * requests upload from and write to: fewer, larger pages leave the device
+ * fewer address translations to make (uploads from page-locked memory
+ * allocated buffer by buffer were measured to stall for milliseconds at
+ * times; from such regions less often).  *ptr receives a 256-byte-aligned
+ * block of at least `bytes` bytes (host, owned by the caller until
+ * pf_host_free).  PF_EINVAL for bytes == 0 or a null ptr, PF_ENOMEM if a
+ * region cannot be mapped, PF_ECUDA if registering it fails.  Needs no
+ * context; thread-safe. */
+PF_API pf_status pf_host_alloc(size_t bytes, void **ptr);
+
+/* Release a block of pf_host_alloc (NULL is a no-op); PF_EINVAL for any
+ * other pointer.  No GPU work may still use it. */
+PF_API pf_status pf_host_free(void *ptr);
+
 /* ---- a7: the whole path on host buffers, chunked and graph-replayed ------ */
 
 /* Pack, filter, compact and verify n pairs held in HOST memory, chunk by

@@ -26,6 +26,7 @@ __all__ = [
     "PF_SHD_STREAK", "pf_set_small_batch", "pf_tune_batch", "pf_set_resolve_by_bounds",
     "pf_last_verified_count", "pf_peak_int", "PF_SERVE_BATCHED", "PF_SERVE_DEVICE_LOOP",
     "pf_serve_trace", "pf_filter_plain_exact", "pf_pack_layout_grouped", "pf_pack_starts",
+    "pf_host_alloc", "pf_host_free", "host_empty",
 ]
 
 PF_SNEAKYSNAKE = 1
@@ -114,6 +115,8 @@ def load():
         "pf_pack_layout": [P, I64, P, ctypes.POINTER(ctypes.c_int64)],
         "pf_pack": [P, P, P, P, I64, P, P, P],
         "pf_pack_layout_grouped": [P, P, I64, P, ctypes.POINTER(ctypes.c_int64)],
+        "pf_host_alloc": [ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p)],
+        "pf_host_free": [P],
         "pf_pack_starts": [P, P, P, P, I64, P, P, P],
         "pf_pack_fixed": [P, P, I64, I, P, P, P],
         "pf_filter": [P, U, ctypes.POINTER(_Pairs), P, P, I, P, P, I64],
@@ -272,6 +275,31 @@ def pf_pack_layout(byte_off):
     _check(load().pf_pack_layout(ctypes.c_void_p(bo.ctypes.data), nseq,
                                  ctypes.c_void_p(wo.ctypes.data), ctypes.byref(total)))
     return wo, int(total.value)
+
+
+def pf_host_alloc(nbytes):
+    """Page-locked host block of at least nbytes (huge pages where the
+    system has them); returns its address.  Free with pf_host_free."""
+    p = ctypes.c_void_p()
+    _check(load().pf_host_alloc(ctypes.c_size_t(int(nbytes)), ctypes.byref(p)))
+    return p.value
+
+
+def pf_host_free(addr):
+    _check(load().pf_host_free(ctypes.c_void_p(addr)))
+
+
+def host_empty(count, dtype):
+    """A numpy array of `count` elements in pf_host_alloc memory, freed when
+    the last view of it goes away."""
+    import numpy as np
+    import weakref
+    dt = np.dtype(dtype)
+    nbytes = max(int(count) * dt.itemsize, 1)
+    addr = pf_host_alloc(nbytes)
+    raw = (ctypes.c_uint8 * nbytes).from_address(addr)
+    weakref.finalize(raw, pf_host_free, addr)
+    return np.frombuffer(raw, dtype=np.uint8)[:int(count) * dt.itemsize].view(dt)
 
 
 def pf_pack_layout_grouped(byte_off, E=None):
@@ -577,8 +605,9 @@ def pf_serve_start(ctx, hbm_budget=0, max_requests=0, chunk_pairs=0, workers=0,
 class Request:
     """A request in host memory (numpy arrays).  The arrays are kept
     referenced here until the request is waited for.  pinned=True copies the
-    inputs into, and allocates the outputs in, page-locked memory (the fast
-    path: asynchronous uploads, results written in place by the GPU)."""
+    inputs into, and allocates the outputs in, page-locked memory from
+    pf_host_alloc (the fast path: asynchronous uploads, results written in
+    place by the GPU)."""
 
     def __init__(self, deciders, reads, refs, byte_off, E, pinned=False):
         import numpy as np
@@ -586,17 +615,18 @@ class Request:
         def host(a, dtype):
             a = np.ascontiguousarray(a, dtype=dtype)
             if pinned:
-                t = torch.from_numpy(a.copy() if a.size else np.zeros(1, dtype)).pin_memory()
-                self._keep.append(t)
-                return t.numpy()[:a.size]
+                h = host_empty(a.size, dtype)
+                h[:] = a
+                return h
             return a
 
         def zeros(count, dtype):
+            dt = torch.empty(0, dtype=dtype).numpy().dtype
             if pinned:
-                t = torch.zeros(count, dtype=dtype).pin_memory()
-                self._keep.append(t)
-                return t.numpy()
-            return np.zeros(count, dtype=torch.empty(0, dtype=dtype).numpy().dtype)
+                h = host_empty(count, dt)
+                h[:] = 0
+                return h
+            return np.zeros(count, dtype=dt)
 
         self._keep = []
         self.reads = host(reads, np.uint8)

@@ -93,3 +93,15 @@ def test_grouped_layout_host_helper():
     with pytest.raises(pf.PFError):
         pf.pf_pack_layout_grouped(np.array([0, 5, 9], dtype=np.int64),
                                   np.array([-1, 0], dtype=np.int16))
+
+
+def test_host_alloc_argument_checks_without_gpu():
+    """pf_host_alloc and pf_host_free refuse bad arguments before touching
+    CUDA."""
+    import paper_1910_03936_gb300 as pf
+    lib = pf.load()
+    p = ctypes.c_void_p()
+    assert lib.pf_host_alloc(ctypes.c_size_t(0), ctypes.byref(p)) == 1   # PF_EINVAL
+    assert lib.pf_host_alloc(ctypes.c_size_t(16), None) == 1
+    assert lib.pf_host_free(None) == 0
+    assert lib.pf_host_free(ctypes.c_void_p(0x1000)) == 1

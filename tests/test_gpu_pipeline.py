@@ -59,3 +59,37 @@ def test_pinned_host_buffers(pf, ctx):
     oa, oc, od = expected(P, 3)
     assert np.array_equal(cnt, oc) and np.array_equal(acc, oa)
     assert np.array_equal(dist, od)
+
+
+def test_huge_page_host_buffers(pf, ctx):
+    """Inputs and outputs in pf_host_alloc memory: the same results; the
+    block is page-locked (the CUDA runtime sees host memory) and 256-byte
+    aligned; a freed block's space is reused; freeing an unknown pointer is
+    refused."""
+    import ctypes
+    import torch
+    P = synth.generate(synth.MIXED, 24, 5003)
+    reads = pf.host_empty(P.reads.size, np.uint8)
+    reads[:] = P.reads
+    refs = pf.host_empty(P.refs.size, np.uint8)
+    refs[:] = P.refs
+    off = pf.host_empty(P.read_off.size, np.int64)
+    off[:] = P.read_off
+    E = pf.host_empty(P.E.size, np.int16)
+    E[:] = P.E
+    out = (pf.host_empty(2 * P.n, np.uint8), pf.host_empty(2 * P.n, np.int16),
+           pf.host_empty(P.n, np.int32))
+    assert reads.ctypes.data % 256 == 0
+    assert torch.from_numpy(reads).is_pinned()
+    acc, cnt, dist = pf.pf_run_host(ctx, 3, reads, refs, int(P.E.max()), byte_off=off, E=E,
+                                    chunk_pairs=2048, out=out)
+    oa, oc, od = expected(P, 3)
+    assert np.array_equal(cnt, oc) and np.array_equal(acc, oa)
+    assert np.array_equal(dist, od)
+    addr = pf.pf_host_alloc(3 << 20)
+    pf.pf_host_free(addr)
+    assert pf.pf_host_alloc(3 << 20) == addr  # first fit: the same space again
+    pf.pf_host_free(addr)
+    with pytest.raises(pf.PFError):
+        pf.pf_host_free(addr)  # already freed: unknown
+    pf.pf_host_free(None)
