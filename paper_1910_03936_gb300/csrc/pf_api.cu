@@ -145,9 +145,17 @@ __global__ void bin_scan_kernel(const unsigned long long *hist, int64_t *bin_sta
     if (lane == 0) *ident = (used <= 1);
 }
 
-// Each block claims room for its pairs per key with one atomic per key and
-// places its pairs there (order inside a block's share is arbitrary; every
-// pair keeps its own index, so results do not depend on it).
+// Each block takes tiles of 2,048 pairs, 8 rounds of 256 consecutive pairs
+// (one per thread), ranks them per key in shared memory and claims room for
+// the tile's pairs per key with one global atomic per key.  Large tiles
+// keep the contended global cursors (one per key, a few dozen in use) to a
+// few atomics per 2,048 pairs.  Order inside a tile's share follows the
+// order in which the warps' atomics land: a warp's pairs of one key keep
+// their order, so a bin's pairs stay in runs of consecutive pairs (which a
+// layout grouped by threshold and length keeps side by side in memory).
+// Results do not depend on it: every pair keeps its own index.
+constexpr int kScatterPer = 8;
+
 __global__ void __launch_bounds__(256)
 bin_scatter_kernel(const int16_t *E, const int32_t *lens, int64_t n, int E_max, BinTable t,
                    unsigned long long *cursor, int64_t *order, const int *ident) {
@@ -156,24 +164,26 @@ bin_scatter_kernel(const int16_t *E, const int32_t *lens, int64_t n, int E_max, 
     __shared__ int tab[PF_MAX_E + 1];
     if (*ident) return;
     stage_keys(t, tab);
-    for (int64_t p0 = (int64_t)blockIdx.x * blockDim.x; p0 < n;
-         p0 += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = p0 + threadIdx.x;
+    constexpr int64_t kTile = 256 * kScatterPer;
+    for (int64_t t0 = (int64_t)blockIdx.x * kTile; t0 < n; t0 += (int64_t)gridDim.x * kTile) {
         for (int i = threadIdx.x; i < kNumBinKeys; i += blockDim.x) cnt[i] = 0;
         __syncthreads();  // tab staged; cnt zeroed
-        const int lane = threadIdx.x & 31;
-        const int key = p < n ? key_of(__ldg(E + p), __ldg(lens + p), E_max, tab) : -1;
-        const unsigned peers = __match_any_sync(0xffffffffu, key);
-        const int leader = __ffs(peers) - 1;
-        unsigned r0 = 0;
-        if (key >= 0 && lane == leader) r0 = atomicAdd(&cnt[key], (unsigned)__popc(peers));
-        const unsigned rank =
-            __shfl_sync(0xffffffffu, r0, leader) + __popc(peers & ((1u << lane) - 1u));
+        const int64_t p0 = t0 + threadIdx.x;
+        int key[kScatterPer];
+        unsigned rank[kScatterPer];
+#pragma unroll
+        for (int k = 0; k < kScatterPer; ++k) {
+            const int64_t p = p0 + k * 256;
+            key[k] = p < n ? key_of(__ldg(E + p), __ldg(lens + p), E_max, tab) : -1;
+            rank[k] = key[k] >= 0 ? atomicAdd(&cnt[key[k]], 1u) : 0u;
+        }
         __syncthreads();
         for (int i = threadIdx.x; i < kNumBinKeys; i += blockDim.x)
             base[i] = cnt[i] ? atomicAdd(&cursor[i], (unsigned long long)cnt[i]) : 0ull;
         __syncthreads();
-        if (p < n) order[base[key] + rank] = p;
+#pragma unroll
+        for (int k = 0; k < kScatterPer; ++k)
+            if (key[k] >= 0) order[base[key[k]] + rank[k]] = p0 + k * 256;
         __syncthreads();  // cnt and base are reused by the next tile
     }
 }
@@ -386,13 +396,12 @@ pf_status pf_ctx::run_batched(unsigned dec, const FilterArgs &a, const Scratch &
     if (single < 0) {
         BinTable t;
         for (int e = 0; e <= PF_MAX_E; ++e) t.cfg_of_E[e] = tune_cfg[dec][std::min(e, a.E_max)];
-        int64_t hb = std::min<int64_t>((a.n + 255) / 256, (int64_t)sms * 8);
         const int64_t hh = std::min<int64_t>((a.n + 256 * kHistPer - 1) / (256 * kHistPer),
                                              (int64_t)sms * 8);
         bin_hist_kernel<<<(unsigned)std::max<int64_t>(hh, 1), 256, 0, stream>>>(
             a.E, a.lens, a.n, a.E_max, t, s.hist);
         bin_scan_kernel<<<1, 32, 0, stream>>>(s.hist, s.bin_start, s.cursor, s.ident);
-        bin_scatter_kernel<<<(unsigned)std::max<int64_t>(hb, 1), 256, 0, stream>>>(
+        bin_scatter_kernel<<<(unsigned)std::max<int64_t>(hh, 1), 256, 0, stream>>>(
             a.E, a.lens, a.n, a.E_max, t, s.cursor, s.order, s.ident);
     }
     pf_status st = cuda(cudaGetLastError(), "binning launch");
@@ -813,13 +822,12 @@ pf_status pf_tune_batch(pf_ctx *ctx, unsigned deciders, const pf_pairs *pairs,
     // group the pairs by threshold: bin e holds the pairs with E = e
     BinTable t;
     for (int e = 0; e <= PF_MAX_E; ++e) t.cfg_of_E[e] = e;
-    const int64_t hb = std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)ctx->sms * 8));
     bin_init_kernel<<<1, 32, 0, ctx->stream>>>(s.bin_start, s.work, s.hist, kNumBatchCfgs, -1, n);
     const int64_t hh = std::max<int64_t>(
         1, std::min<int64_t>((n + 256 * kHistPer - 1) / (256 * kHistPer), (int64_t)ctx->sms * 8));
     bin_hist_kernel<<<(unsigned)hh, 256, 0, ctx->stream>>>(E, lens, n, E_max, t, s.hist);
     bin_scan_kernel<<<1, 32, 0, ctx->stream>>>(s.hist, s.bin_start, s.cursor, s.ident);
-    bin_scatter_kernel<<<(unsigned)hb, 256, 0, ctx->stream>>>(E, lens, n, E_max, t, s.cursor,
+    bin_scatter_kernel<<<(unsigned)hh, 256, 0, ctx->stream>>>(E, lens, n, E_max, t, s.cursor,
                                                                s.order, s.ident);
     int64_t starts[PF_MAX_E + 2];
     std::vector<unsigned long long> keys(kNumBinKeys);
