@@ -648,7 +648,7 @@ __global__ void __launch_bounds__(kSplitWarps * 32, (XE <= 7 ? 5 : (XE <= 10 ? 4
 // The walk is split_sneakysnake's, with the group's lanes each folding their
 // own diagonals into T.
 template <int TPP, int DPT>
-__device__ __forceinline__ int split_sneakysnake_group(const uint32_t *mine, int W, int E, int g,
+__device__ __forceinline__ int split_sneakysnake_group(const uint32_t *mine, int W, int E,
                                                        unsigned gmask, uint32_t neg1) {
     if (W == 0) return 0;
     // slots outside the band were stored as all ones (PairFilter::ONES):
@@ -701,7 +701,7 @@ __device__ __forceinline__ void filter_split_group_pair(const FilterArgs &a, int
     st.run(a.pairs, g, gmask);
     int ssc = 0, gkc = 0;
     st.finish(g, gmask, &ssc, &gkc);
-    if constexpr (DEC & 1) ssc = split_sneakysnake_group<TPP, DPT>(mine, W, E, g, gmask, st.neg1);
+    if constexpr (DEC & 1) ssc = split_sneakysnake_group<TPP, DPT>(mine, W, E, gmask, st.neg1);
     if (g == 0) write_outputs<DEC>(a, p, E, ssc, gkc, st.h);
 }
 
