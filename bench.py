@@ -478,6 +478,17 @@ def other_configs(pf, args, rank):
         out[name] = row
         del reads, refs, rd, rf, pairs, acc, cnt, dist, P
         torch.cuda.empty_cache()
+    if not args.no_sweep:
+        # configuration 2's sweep of E = 0..15 on 2M-pair samples of its
+        # 20M-pair batches (compact: pairs/s only)
+        rows = threshold_sweep_rows(pf, ctx, 2_000_000, lambda fn, reps: timed(fn, reps), dev, 5)
+        out["cfg2_sweep_2M_samples_of_20M"] = {
+            "E": {int(E): {"sneakysnake_batched_pairs_s": r["ss_batched_pairs_s"],
+                           "sneakysnake_plain_pairs_s": r["ss_plain_pairs_s"],
+                           "batched_over_plain": round(r["batched_over_plain"], 3),
+                           "step_pairs_s": r["step_pairs_s"]} for E, r in rows.items()},
+            "step": "pack x2 + filter (both deciders) + compact + verify"}
+        torch.cuda.empty_cache()
     pf.pf_destroy(ctx)
     return out
 
@@ -486,14 +497,12 @@ def other_configs(pf, args, rank):
 # the other configurations (their own lines; the default line is the
 # 150 bp, E = 6 workload above)
 
-def run_threshold_sweep(args, pf, ctx, timed, dev):
-    """150 bp pairs at every threshold E = 0..15, one batch per E (the same
-    recipe as the headline batch, seed 0x5EED0002 + E): SneakySnake alone
-    batched (tuned) vs plain, and the step of both deciders with
-    verification.  One JSON line per E, then a summary line."""
+def threshold_sweep_rows(pf, ctx, n, timed, dev, reps, emit=None):
+    """150 bp pairs at every threshold E = 0..15, one batch of n pairs per E
+    (the headline recipe, seed 0x5EED0002 + E): SneakySnake alone batched
+    (tuned) vs plain, and the step of both deciders with verification."""
     import torch
     import synth
-    n = args.pairs
     W = (M + 31) // 32
     rd = pf.Seqs.empty(n * W, dev, stride_words=W)
     rf = pf.Seqs.empty(n * W, dev, stride_words=W)
@@ -502,7 +511,6 @@ def run_threshold_sweep(args, pf, ctx, timed, dev):
     acc = torch.empty(2 * n, dtype=torch.uint8, device=dev)
     cnt = torch.empty(2 * n, dtype=torch.int16, device=dev)
     dist = torch.empty(n, dtype=torch.int32, device=dev)
-    reps = max(1, args.steps)
     rows = {}
     for E in range(16):
         P = synth.generate(synth.SKEWED, 0x5EED0002 + E, n, m=M, E=E, kmax=KMAX)
@@ -527,8 +535,18 @@ def run_threshold_sweep(args, pf, ctx, timed, dev):
                "accepted_frac": float(acc[:n].float().mean().item()),
                "verified_frac": n_ver / n}
         rows[E] = row
-        print(json.dumps(row), flush=True)
+        if emit:
+            emit(row)
         del reads, refs
+    return rows
+
+
+def run_threshold_sweep(args, pf, ctx, timed, dev):
+    """The sweep of every threshold at the headline size: one JSON line per
+    E, then a summary line."""
+    n = args.pairs
+    rows = threshold_sweep_rows(pf, ctx, n, timed, dev, max(1, args.steps),
+                                emit=lambda r: print(json.dumps(r), flush=True))
     print(json.dumps({"workload": "cfg2_sweep", "read_len": M, "pairs_per_E": n,
                       "step": "pack x2 + filter (both deciders) + compact + verify",
                       "rows": rows}), flush=True)
@@ -1073,6 +1091,8 @@ def main():
                     help="time one filter kernel instead of the step (profiling)")
     ap.add_argument("--deciders", type=int, default=3)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the compact E = 0..15 sweep in the configs block")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the compact rows of configurations 1, 3 and 4")
     ap.add_argument("--workload", default="headline",
