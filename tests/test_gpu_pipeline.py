@@ -86,10 +86,16 @@ def test_huge_page_host_buffers(pf, ctx):
     oa, oc, od = expected(P, 3)
     assert np.array_equal(cnt, oc) and np.array_equal(acc, oa)
     assert np.array_equal(dist, od)
-    addr = pf.pf_host_alloc(3 << 20)
-    pf.pf_host_free(addr)
-    assert pf.pf_host_alloc(3 << 20) == addr  # first fit: the same space again
-    pf.pf_host_free(addr)
+    import gc
+    gc.collect()
+    gc.disable()  # no finalizer frees other blocks between the calls below
+    try:
+        addr = pf.pf_host_alloc(3 << 20)
+        pf.pf_host_free(addr)
+        assert pf.pf_host_alloc(3 << 20) == addr  # first fit: the same space again
+        pf.pf_host_free(addr)
+    finally:
+        gc.enable()
     with pytest.raises(pf.PFError):
         pf.pf_host_free(addr)  # already freed: unknown
     pf.pf_host_free(None)
