@@ -186,8 +186,12 @@ PF_API pf_status pf_pack_fixed(pf_ctx *ctx, const uint8_t *ascii, int64_t nseq, 
 /* ---- a2-a4, a7: filtering ----------------------------------------------- */
 
 /* Neighbourhood map + deciders for n pairs through the batch scheduler:
- * pairs are grouped by threshold, each group runs the tuned mapping
- * (threads per pair, work chunk) in one persistent launch.
+ * pairs are grouped by the configuration their threshold is tuned to and,
+ * inside a group, by length class (ceil(len/32) words); each group runs the
+ * tuned mapping (threads per pair, work chunk) in one persistent launch.
+ * Batches below pf_set_small_batch's size take one plain launch (with one
+ * threshold for the batch, E NULL and E_max <= 15, the plain kernel with
+ * that threshold fixed at compile time).
  *   deciders  PF_SNEAKYSNAKE, PF_GATEKEEPER or both (two output slots)
  *   lens      device int32[n], pair lengths
  *   E         device int16[n] per-pair thresholds, or NULL for E_max for
@@ -228,11 +232,13 @@ PF_API pf_status pf_kernel_configs(int *tpp, int *dpt, int *ecap, int *exact_e, 
                                    int cap, int *count);
 
 /* Autotune on a batch as it is: its pairs are grouped by threshold (E,
- * device int16[n], required), and for every threshold with at least 1,024
- * pairs each configuration serving it (and work items of 64, 256 and 1,024
- * pairs) is timed on up to `sample` of that threshold's own pairs (0 =
- * 2^20), reps timed runs each after one warm-up; the fastest becomes the
- * scheduler's choice for (deciders, E).  Thresholds with fewer pairs keep
+ * device int16[n], required) and length class, as the scheduler groups
+ * them, and for every threshold with at least 1,024 pairs each
+ * configuration serving it (and work items of 64, 256 and 1,024 pairs) is
+ * timed on up to `sample` of that threshold's own pairs (0 = 2^20; the
+ * same share of each of its length classes, each share a run of the class
+ * in the scheduler's order), reps timed runs each after one warm-up; the
+ * fastest becomes the scheduler's choice for (deciders, E).  Thresholds with fewer pairs keep
  * their choice.  Synchronises the context stream; allocates its output
  * buffers (freed on return).  PF_EINVAL as pf_filter, or for n <= 0,
  * reps <= 0, sample < 0 or a NULL E. */
