@@ -438,8 +438,9 @@ PF_API pf_status pf_host_free(void *ptr);
  *   E            host int16[n], or NULL for E_max for every pair
  *   accept, count, dist  host outputs as in pf_filter_verify
  *   chunk_pairs  pairs per chunk (>= 1; 0 = 2^20)
- * Page-locked host buffers are copied asynchronously; pageable ones work
- * but serialise the copies.  Allocates its slot buffers (freed on return). */
+ * Page-locked host buffers (pf_host_alloc's, or any registered memory)
+ * are copied asynchronously; pageable ones work but serialise the copies.
+ * Allocates its slot buffers (freed on return). */
 PF_API pf_status pf_run_host(pf_ctx *ctx, unsigned deciders, const uint8_t *reads,
                              const uint8_t *refs, const int64_t *byte_off, int len,
                              const int16_t *E, int E_max, uint8_t *accept, int16_t *count,
